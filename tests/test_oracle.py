@@ -1,0 +1,350 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here touches the CUDA library.  Each test pins the oracle to a fact
+that does not come from the oracle itself: the paper's worked example
+(Fig. 1), known counts of digraph classes, the orbit-stabilizer identity,
+brute force over all vertex subsets, closed forms on hand-worked graphs,
+textbook invariants (triangles via a sparse matrix product) and the G(n,p)
+expectation of Eq. 4.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from conftest import read_golden
+from oracle import oracle as O
+from paper_2201_11655_b300 import synth
+
+
+def col_of(k, canon_mask):
+    canon, _ = O.classes(k)
+    hit = np.nonzero(canon == canon_mask)[0]
+    assert hit.size == 1, canon_mask
+    return int(hit[0])
+
+
+# ---------------------------------------------------------------- classes --
+
+def test_fig1_index_and_minimum():
+    g = read_golden("fig1_motif_index.txt")
+    k = int(g["k"][0])
+    rows = g["rows"]
+    bits = "".join(rows[i][j] for i in range(k) for j in range(k) if i != j)
+    assert bits == g["bitstring"][0]
+    idx = int(bits, 2)
+    assert idx == int(g["index"][0])
+    assert O.canonical_index(k, idx) == int(g["index_min"][0])
+
+
+def test_fig1_isomorphs():
+    # The three labelled isomorphs of the Fig. 1 motif are 53, 30 and 43; all
+    # map to 30 and no other index does.
+    members = [i for i in range(64) if O.canonical_index(3, i) == 30]
+    assert members == [30, 43, 53]
+
+
+def test_class_counts_known():
+    # Weakly connected digraphs up to isomorphism on 3 / 4 nodes: 13 / 199
+    # (OEIS A003085); all digraphs: 16 / 218 (OEIS A000273); labelled weakly
+    # connected digraphs: 54 / 3834 (OEIS A003027).
+    for k, nconn, nall, nlab in ((3, 13, 16, 54), (4, 199, 218, 3834)):
+        canon, niso = O.classes(k)
+        assert len(canon) == nconn
+        assert int(niso.sum()) == nlab
+        canon_all, niso_all = O.classes(k, connected_only=False)
+        assert len(canon_all) == nall
+        assert int(niso_all.sum()) == 2 ** (k * (k - 1))
+        assert np.all(np.diff(canon) > 0)
+
+
+def _matrix(k, idx):
+    m = np.zeros((k, k), np.int64)
+    b = k * (k - 1) - 1
+    for i in range(k):
+        for j in range(k):
+            if i != j:
+                m[i, j] = (idx >> b) & 1
+                b -= 1
+    return m
+
+
+def test_orbit_stabilizer():
+    # N_Iso(m) * |Aut(m)| = k! for every class (orbit-stabilizer theorem);
+    # |Aut| is counted here directly on the adjacency matrix.
+    for k in (3, 4):
+        canon, niso = O.classes(k)
+        for c, ni in zip(canon, niso):
+            m = _matrix(k, int(c))
+            aut = sum(1 for p in itertools.permutations(range(k))
+                      if np.array_equal(m[np.ix_(p, p)], m))
+            assert ni * aut == math.factorial(k)
+
+
+def test_canonical_is_minimum_of_own_orbit():
+    # Every index is >= its canonical index, and applying a permutation never
+    # changes the canonical index.
+    rng = np.random.default_rng(0)
+    for k in (3, 4):
+        for idx in rng.integers(0, 2 ** (k * (k - 1)), 200):
+            c = O.canonical_index(k, int(idx))
+            assert c <= idx
+            m = _matrix(k, int(idx))
+            p = rng.permutation(k)
+            pm = m[np.ix_(p, p)]
+            bits = "".join(str(pm[i, j]) for i in range(k) for j in range(k) if i != j)
+            assert O.canonical_index(k, int(bits, 2)) == c
+
+
+# ------------------------------------------------------- enumeration pins --
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_esu_equals_brute_force_random(k):
+    rng = np.random.default_rng(1234 + k)
+    for trial in range(60):
+        n = int(rng.integers(k, 14 if k == 4 else 22))
+        p = float(rng.uniform(0.05, 0.6))
+        n, s, d = synth.gnp(n, p, int(rng.integers(0, 2**31)))
+        a, ga = O.count(n, s, d, k, threads=2)
+        b, gb = O.count_brute(n, s, d, k)
+        assert ga == gb
+        np.testing.assert_array_equal(a, b)
+
+
+def test_esu_equals_brute_force_gnp100():
+    # The small benchmark workload itself, k = 3 and k = 4, two independent
+    # enumerations.
+    n, s, d = synth.gnp(100, 0.08, 0)
+    for k in (3, 4):
+        a, ga = O.count(n, s, d, k)
+        b, gb = O.count_brute(n, s, d, k)
+        assert ga == gb
+        np.testing.assert_array_equal(a, b)
+
+
+def test_self_loops_and_duplicates_ignored():
+    n, s, d = synth.gnp(30, 0.2, 5)
+    a, _ = O.count(n, s, d, 4)
+    s2 = np.concatenate([s, s[:40], np.arange(10)])
+    d2 = np.concatenate([d, d[:40], np.arange(10)])
+    b, _ = O.count(n, s2, d2, 4)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_csr_example_k3_hand_worked():
+    # The CSR example graph: arcs 0>1 0>2 0>3 2>0 3>1 3>2.  Its four 3-sets are
+    # all connected.  By hand: {0,1,2} is a mutual pair plus an out-arc
+    # (minimum index 7), {0,1,3} a transitive triangle (11), {0,2,3} a mutual
+    # pair plus a 2-path closing it (27), {1,2,3} an out-star from 3 (3).
+    g = read_golden("csr_example.txt")
+    arcs = [tuple(int(x) for x in a.split(">")) for a in g["arcs"]]
+    s = np.array([a for a, _ in arcs]); d = np.array([b for _, b in arcs])
+    out, found = O.count(4, s, d, 3)
+    assert found == 4
+    want = np.zeros((4, 13), np.uint64)
+    for members, mask in (((0, 1, 2), 7), ((0, 1, 3), 11), ((0, 2, 3), 27), ((1, 2, 3), 3)):
+        for v in members:
+            want[v, col_of(3, mask)] += 1
+    np.testing.assert_array_equal(out, want)
+    out4, found4 = O.count(4, s, d, 4)
+    assert found4 == 1
+    # the whole graph is one 4-set; its class is the canonical form of its
+    # own index under the identity order
+    idx = int("".join("1" if (i, j) in arcs else "0"
+                      for i in range(4) for j in range(4) if i != j), 2)
+    c = col_of(4, O.canonical_index(4, idx))
+    assert (out4[:, c] == 1).all() and out4.sum() == 4
+
+
+def _arcs(pairs):
+    pairs = list(pairs)
+    return np.array([p[0] for p in pairs], np.int32), np.array([p[1] for p in pairs], np.int32)
+
+
+@pytest.mark.parametrize("n", [4, 5, 7])
+def test_complete_digraph(n):
+    s, d = _arcs((i, j) for i in range(n) for j in range(n) if i != j)
+    out3, _ = O.count(n, s, d, 3)
+    out4, _ = O.count(n, s, d, 4)
+    assert (out3[:, col_of(3, 63)] == math.comb(n - 1, 2)).all() and out3.sum() == n * math.comb(n - 1, 2)
+    assert (out4[:, col_of(4, 4095)] == math.comb(n - 1, 3)).all() and out4.sum() == n * math.comb(n - 1, 3)
+
+
+def test_directed_cycles():
+    for n in (3, 4, 5, 8):
+        s, d = _arcs((i, (i + 1) % n) for i in range(n))
+        out3, _ = O.count(n, s, d, 3)
+        if n == 3:
+            assert (out3[:, col_of(3, 25)] == 1).all() and out3.sum() == 3
+        else:
+            # every vertex starts, ends and is the middle of one directed 2-path
+            assert (out3[:, col_of(3, 6)] == 3).all() and out3.sum() == 3 * n
+        if n >= 4:
+            out4, _ = O.count(n, s, d, 4)
+            if n == 4:
+                assert (out4[:, col_of(4, 674)] == 1).all() and out4.sum() == 4
+            else:
+                assert (out4[:, col_of(4, 84)] == 4).all() and out4.sum() == 4 * n
+
+
+@pytest.mark.parametrize("L", [3, 4, 9])
+def test_stars(L):
+    out_s, out_d = _arcs((0, i) for i in range(1, L + 1))
+    n = L + 1
+    for (s, d), m3, m4 in (((out_s, out_d), 3, 7), ((out_d, out_s), 10, 292)):
+        o3, _ = O.count(n, s, d, 3)
+        o4, _ = O.count(n, s, d, 4)
+        c3, c4 = col_of(3, m3), col_of(4, m4)
+        assert o3[0, c3] == math.comb(L, 2) and (o3[1:, c3] == L - 1).all()
+        assert o3.sum() == 3 * math.comb(L, 2)
+        assert o4[0, c4] == math.comb(L, 3) and (o4[1:, c4] == math.comb(L - 1, 2)).all()
+        assert o4.sum() == 4 * math.comb(L, 3)
+
+
+def test_transitive_tournament():
+    # "regular DAG" of the toy-graph validations: i -> j for all i < j.
+    n = 6
+    s, d = _arcs((i, j) for i in range(n) for j in range(i + 1, n))
+    o3, _ = O.count(n, s, d, 3)
+    o4, _ = O.count(n, s, d, 4)
+    assert (o3[:, col_of(3, 11)] == math.comb(n - 1, 2)).all() and o3.sum() == 3 * math.comb(n, 3)
+    c4 = int(np.nonzero(o4[0])[0][0])
+    assert (o4[:, c4] == math.comb(n - 1, 3)).all() and o4.sum() == 4 * math.comb(n, 4)
+
+
+# ------------------------------------------------------------ invariants --
+
+def _undirected(n, s, d):
+    A = sp.coo_matrix((np.ones(s.size), (s, d)), shape=(n, n)).tocsr()
+    U = ((A + A.T) > 0).astype(np.int64)
+    U.setdiag(0)
+    U.eliminate_zeros()
+    return U.tocsr()
+
+
+def test_k3_totals_and_triangles():
+    # Connected 3-sets through v: C(d_v, 2) + sum_{a in N(v)} (d_a - 1) - 2 tri(v);
+    # the classes whose G_U is a triangle sum to tri(v) = (U^2 o U)_vv / 2.
+    n, s, d = synth.chung_lu(400, 4.0, 2.3, 7, reciprocity=0.3)
+    U = _undirected(n, s, d)
+    deg = np.asarray(U.sum(axis=1)).ravel()
+    tri = np.asarray((U @ U).multiply(U).sum(axis=1)).ravel() // 2
+    nbr_sum = U @ (deg - 1)
+    out, found = O.count(n, s, d, 3)
+    tot = out.sum(axis=1).astype(np.int64)
+    np.testing.assert_array_equal(tot, deg * (deg - 1) // 2 + nbr_sum - 2 * tri)
+    canon, _ = O.classes(3)
+    # triangle classes: all three unordered pairs carry at least one arc
+    tri_cols = []
+    for c, m in enumerate(canon):
+        M = _matrix(3, int(m))
+        if all(M[i, j] or M[j, i] for i, j in ((0, 1), (0, 2), (1, 2))):
+            tri_cols.append(c)
+    np.testing.assert_array_equal(out[:, tri_cols].sum(axis=1).astype(np.int64), tri)
+    assert out.sum() == 3 * found
+
+
+def test_sum_over_vertices_is_k_times_global():
+    n, s, d = synth.gnp(60, 0.1, 11)
+    for k in (3, 4):
+        out, found = O.count(n, s, d, k)
+        assert int(out.sum()) == k * found
+
+
+def _transpose_map(k):
+    canon, _ = O.classes(k)
+    m = {}
+    for c, mask in enumerate(canon):
+        M = _matrix(k, int(mask)).T
+        bits = "".join(str(M[i, j]) for i in range(k) for j in range(k) if i != j)
+        m[c] = col_of(k, O.canonical_index(k, int(bits, 2)))
+    return np.array([m[c] for c in range(len(canon))])
+
+
+def test_transpose_permutes_columns():
+    n, s, d = synth.chung_lu(200, 3.0, 2.5, 3, reciprocity=0.2)
+    for k in (3, 4):
+        a, _ = O.count(n, s, d, k)
+        b, _ = O.count(n, d, s, k)
+        t = _transpose_map(k)
+        want = np.zeros_like(a)
+        want[:, t] = a
+        np.testing.assert_array_equal(b, want)
+
+
+def test_relabel_permutes_rows():
+    n, s, d = synth.gnp(80, 0.07, 21)
+    perm = np.random.default_rng(3).permutation(n).astype(np.int32)
+    for k in (3, 4):
+        a, _ = O.count(n, s, d, k)
+        b, _ = O.count(n, perm[s], perm[d], k)
+        np.testing.assert_array_equal(b[perm], a)
+
+
+def test_disjoint_union_concatenates_rows():
+    n1, s1, d1 = synth.gnp(40, 0.1, 1)
+    n2, s2, d2 = synth.chung_lu(50, 3.0, 2.5, 2)
+    a1, _ = O.count(n1, s1, d1, 4)
+    a2, _ = O.count(n2, s2, d2, 4)
+    b, _ = O.count(n1 + n2, np.concatenate([s1, s2 + n1]), np.concatenate([d1, d2 + n1]), 4)
+    np.testing.assert_array_equal(b, np.vstack([a1, a2]))
+
+
+def test_degree_rank_definition():
+    n, s, d = synth.chung_lu(300, 3.0, 2.3, 9, reciprocity=0.2)
+    U = _undirected(n, s, d)
+    deg = np.asarray(U.sum(axis=1)).ravel()
+    order = np.lexsort((np.arange(n), -deg))
+    rank = O.degree_rank(n, s, d)
+    np.testing.assert_array_equal(rank[order], np.arange(n))
+
+
+def test_root_ranges_partition_the_count():
+    # Lemma 1: a set is counted only from its lowest-ranked member, so disjoint
+    # rank ranges partition the sets.
+    n, s, d = synth.chung_lu(300, 3.0, 2.3, 13, reciprocity=0.2)
+    rank = O.degree_rank(n, s, d)
+    for k in (3, 4):
+        full, gf = O.count(n, s, d, k)
+        acc = np.zeros_like(full)
+        tot = 0
+        for lo, hi in ((0, 5), (5, 40), (40, 41), (41, n)):
+            part, g = O.count_roots(n, s, d, k, rank, lo, hi)
+            acc += part
+            tot += g
+        assert tot == gf
+        np.testing.assert_array_equal(acc, full)
+
+
+# ------------------------------------------------------- G(n,p), Eq. 4 --
+
+@pytest.mark.parametrize("k,seeds", [(3, 200), (4, 60)])
+def test_gnp_expectation_eq4(k, seeds):
+    # Mean per-vertex local count over vertices and seeds of G(100, 0.08)
+    # against Eq. 4 (exact by linearity of expectation).  Classes with a large
+    # expectation: within 5 standard errors of the seed-to-seed spread.
+    # Rare classes: the total over all seeds and vertices stays inside a
+    # generous Poisson tail of the expected total.
+    n, p = 100, 0.08
+    E = O.gnp_expected_local(n, p, k)
+    per_seed = []
+    for seed in range(seeds):
+        nn, s, d = synth.gnp(n, p, 10_000 + seed)
+        out, _ = O.count(nn, s, d, k)
+        per_seed.append(out.astype(np.float64).mean(axis=0))
+    per_seed = np.array(per_seed)
+    mean = per_seed.mean(axis=0)
+    sd = per_seed.std(axis=0, ddof=1)
+    big = E * n * seeds >= 200
+    assert big.sum() >= 5
+    se = sd[big] / math.sqrt(seeds)
+    assert np.all(np.abs(mean[big] - E[big]) <= 5 * se + 1e-12), (mean[big], E[big], se)
+    tot_obs = per_seed[:, ~big].sum(axis=0) * n
+    tot_exp = E[~big] * n * seeds
+    # observed totals are sums of per-vertex credits; each set credits k
+    # vertices, so counts of sets are tot/k.  Poisson bound on sets.
+    sets_obs = tot_obs / k
+    sets_exp = tot_exp / k
+    assert np.all(sets_obs <= sets_exp + 8 * np.sqrt(sets_exp) + 12)
