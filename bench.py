@@ -1,0 +1,326 @@
+"""Benchmark: per-vertex directed k-motif counting on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--k 3|4]
+
+A step is one vdmc_count over the whole graph (every root, every BFS
+structure), with the graph already resident in HBM.  Prints ONE JSON line.
+
+value      connected k-sets counted per second (instances/s), device time
+           measured with CUDA events on the launching stream.
+e2e        the same metric through the public API with HOST buffers: each
+           step builds the graph from pinned host arcs (H2D inside), counts,
+           and copies the uint64 counts back to pinned host memory.
+roofline   HBM roofline of the counting kernel: algorithmic bytes
+           (vdmc_work_bytes) / launch time against the measured copy peak.
+cpu_baseline  the CPU oracle on a bounded root sample of the same graph.
+
+--impl reference times the CPU oracle alone (the reference arm of this
+benchmark), on the host cores, on a bounded sample of the same workload.
+N > 1 (torchrun): N independent replicas, one per GPU (weak scaling); the
+path needs no collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "chunglu_n1M_m10M_a2.3_r0.2"
+METRIC = "k=%d per-vertex motif instances/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--k", type=int, default=4)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle sample time")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("count.cu", "vdmc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2201_11655_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(workload, k):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        e = rec.get("%s/k%d" % (workload, k))
+        if e and e.get("kernel_hash") == kernel_source_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "vdmc_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def oracle_sample(n, s, d, k, target_s, threads=None):
+    """Time the oracle on a contiguous range of root ranks, grown until it takes ~target_s.
+
+    Returns dict(value=instances/s, instances, seconds, sample=str, cores)."""
+    from oracle import oracle as O
+    threads = threads or O.default_threads()
+    rank = O.degree_rank(n, s, d)
+    # graph build cost of one oracle call (empty root range), subtracted
+    t0 = time.perf_counter()
+    O.count_roots(n, s, d, k, rank, 0, 0, threads=threads)
+    build_s = time.perf_counter() - t0
+    lo = min(n - 1, max(0, n // 100))
+    w = 64
+    while True:
+        hi = min(n, lo + w)
+        t0 = time.perf_counter()
+        _, found = O.count_roots(n, s, d, k, rank, lo, hi, threads=threads)
+        el = time.perf_counter() - t0 - build_s
+        if el >= target_s or hi >= n or w > n:
+            break
+        w = int(w * max(2.0, min(8.0, target_s / max(el, 1e-3))))
+    return {"value": found / max(el, 1e-9), "instances": int(found), "seconds": el, "cores": threads,
+            "sample": "oracle (ESU + k! canonicalisation, %d threads) on the roots of degree rank [%d, %d) "
+                      "of the same graph: %d connected %d-sets in %.2f s (its own graph build, %.2f s, "
+                      "subtracted)" % (threads, lo, hi, found, k, el, build_s), "lo": lo, "hi": hi}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2201_11655_b300 import synth
+    from oracle import oracle as O
+    n, s, d = synth.workload(args.workload)
+    O.build()
+    threads = O.default_threads()
+    probe = oracle_sample(n, s, d, args.k, max(2.0, args.cpu_seconds / 3))
+    lo, hi = probe["lo"], probe["hi"]
+    rk = O.degree_rank(n, s, d)
+    times, found = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, found = O.count_roots(n, s, d, args.k, rk, lo, hi, threads=threads)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+    sec = sum(times) / len(times)
+    val = found / sec
+    unit = "instances/s"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC % args.k, "value": val, "unit": unit, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": args.k, "n": n, "arcs": int(s.size)},
+        "cpu_baseline": {"value": val, "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": "each step: oracle on the roots of degree rank [%d, %d) (%d connected %d-sets, "
+                                   "graph build included)" % (lo, hi, found, args.k)},
+        "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2201_11655_b300 import build, synth, vdmc
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build.build()
+    vdmc.load()
+    k = args.k
+    C = vdmc.num_classes(k)
+    n, s, d = synth.workload(args.workload)
+    m = int(s.size)
+    stream = torch.cuda.current_stream()
+    src_dev = torch.from_numpy(s).cuda()
+    dst_dev = torch.from_numpy(d).cuda()
+    g = vdmc.graph_create(n, src_dev, dst_dev)
+    info = g.info()
+    del src_dev, dst_dev
+    out = torch.empty((n, C), dtype=torch.uint64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (126 MB)
+
+    for _ in range(args.warmup):
+        vdmc.count(g, k, out)
+    torch.cuda.synchronize()
+    if g.device_status() != 0:
+        raise RuntimeError("device status error after warm-up")
+    total = int(out.view(torch.int64).sum().item())
+    if total % k:
+        raise RuntimeError("sum of per-vertex counts is not a multiple of k")
+    instances = total // k
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local_rank) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()  # evict L2 between timed launches
+            evs[i][0].record(stream)
+            vdmc.count(g, k, out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * instances / (ms / 1e3)
+
+    # e2e through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        src_h = torch.from_numpy(s).pin_memory()
+        dst_h = torch.from_numpy(d).pin_memory()
+        out_h = torch.empty((n, C), dtype=torch.int64).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        tt = []
+        for i in range(1 + e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with vdmc.graph_create(n, src_h, dst_h) as g2:
+                vdmc.count(g2, k, out)
+                out_h.copy_(out.view(torch.int64), non_blocking=True)
+                torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            if i > 0:
+                tt.append(el)
+        e2e_s = sum(tt) / len(tt)
+        e2e = {"value": world * instances / e2e_s, "unit": "instances/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * n * C,
+               "path": "vdmc_graph_create(host arcs) + vdmc_count + D2H of counts"}
+
+    peak, peak_kind = load_peaks()
+    wbytes = g.work_bytes(k)
+    achieved = wbytes / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": load_traffic(args.workload, k), "kernel": "count_kernel<%d>" % k,
+                "algorithmic_bytes_per_launch": wbytes, "peak_kind": "%s hbm_gbs (copy)" % peak_kind}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            smp = oracle_sample(n, s, d, k, args.cpu_seconds)
+            cpu = {"value": smp["value"], "unit": "instances/s", "cores": smp["cores"], "kind": "oracle",
+                   "sample": smp["sample"]}
+        except Exception as ex:  # the oracle is a baseline only
+            cpu = {"value": None, "unit": "instances/s", "cores": None, "kind": "oracle", "sample": "failed: %s" % ex}
+
+    g.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC % k, "value": value, "unit": "instances/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": k, "n": n, "arcs": m, "edges_u": info["edges_u"],
+                       "max_degree": info["max_degree"], "instances_per_step": instances,
+                       "l2": "256 MB buffer written between timed launches (L2 flush)",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "schedule": vdmc.get_schedule()},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+            "cpu_baseline": cpu, "step_ms": step_ms,
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

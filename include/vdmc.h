@@ -1,0 +1,186 @@
+/*
+ * vdmc.h -- C ABI of the B300 (sm_103a) per-vertex directed motif counter.
+ *
+ * The operation (VDMC, arXiv 2201.11655):
+ *   For a directed, unweighted, simple graph G = (V, E) (Definitions) and
+ *   k in {3, 4}, X_{k,m}(i) is the number of vertex sets S with |S| = k and
+ *   i in S such that S is connected in the underlying undirected graph G_U
+ *   and the directed sub-graph induced by S is of motif class m (the
+ *   definition of X_{k,m}(i) in "Comparison to theory in G(n,p)"; the motif
+ *   index of Fig. 1: the k x k adjacency matrix read row-major with the
+ *   diagonal removed, most significant bit first; a class is named by the
+ *   minimum index over its isomorphs, per the isomorph-merge paragraph of
+ *   "The Algorithm").
+ *
+ *   Output columns are the connected classes in ascending order of their
+ *   minimum index: C_3 = 13 columns, C_4 = 199 columns
+ *   (vdmc_class_masks() returns that list).
+ *
+ * Conventions for every call:
+ *   - Vertex ids are int32 in [0, n).  Self-loops are ignored and repeated
+ *     arcs collapsed (the paper assumes a simple graph); both are counted in
+ *     vdmc_graph_info_t.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless documented otherwise.
+ *   - Errors detected on the host are returned at once.  Errors detected in a
+ *     kernel are written to the graph's device status word; read it with
+ *     vdmc_get_device_status() after synchronising the stream.
+ *   - The library never calls exit(), never traps on the device and never
+ *     spins on a device flag.
+ *   - All counts are exact uint64; no floating point is used anywhere.
+ */
+#ifndef VDMC_H
+#define VDMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VDMC_OK = 0,
+    VDMC_ERR_INVALID_ARG = 1,          /* bad k, NULL pointer, negative size, n >= 2^30 */
+    VDMC_ERR_OUT_OF_RANGE_VERTEX = 2,  /* an arc endpoint outside [0, n) */
+    VDMC_ERR_OOM = 3,                  /* device allocation failed */
+    VDMC_ERR_CUDA = 4,                 /* a CUDA runtime call failed */
+    VDMC_ERR_DEVICE_LIMIT = 5,         /* a kernel hit an internal limit (status word) */
+    VDMC_ERR_BUSY = 6                  /* a resource is in use by another call */
+} vdmc_status;
+
+/* Opaque graph: owns its device CSR (degree-ordered ids, 2-bit arc flags
+ * per undirected edge), id maps, task list and work-queue cursor. */
+typedef struct vdmc_graph vdmc_graph;
+
+typedef struct {
+    int32_t n;                 /* vertices */
+    int32_t max_degree;        /* max undirected degree in G_U */
+    int64_t arcs_in;           /* arcs passed to vdmc_graph_create */
+    int64_t self_loops;        /* dropped */
+    int64_t duplicate_arcs;    /* repeated (u,v) collapsed */
+    int64_t arcs_kept;         /* distinct directed arcs */
+    int64_t edges_u;           /* edges of G_U (a reciprocal pair is one edge) */
+    int64_t reciprocal_pairs;  /* edges of G_U carrying arcs both ways */
+    int64_t num_tasks;         /* (root, depth-1 slice) work items */
+    int64_t device_bytes;      /* bytes held on the device by this graph */
+} vdmc_graph_info_t;
+
+/* Launch schedule of the enumeration kernel.  Results never depend on it. */
+typedef struct {
+    int32_t a_chunk;          /* depth-1 neighbours of one root per task (>= 1);
+                                 a root with L such neighbours is split into
+                                 ceil(L / a_chunk) interleaved tasks */
+    int32_t warps_per_block;  /* 1..32 */
+    int32_t blocks_per_sm;    /* 0 = as many as fit */
+    int32_t reserved;
+} vdmc_schedule_t;
+
+/*
+ * Build a graph from a directed arc list (Definitions; CSR paragraph of
+ * "The Algorithm"; degree order of "Vertex ordering and splitting over the
+ * GPU").
+ *   n                 number of vertices, 0 <= n < 2^30
+ *   m                 number of arcs, >= 0
+ *   src, dst          int32[m]: arc e is src[e] -> dst[e].  Host pointers
+ *                     when ptrs_on_device == 0 (copied before the call
+ *                     returns), device pointers otherwise (read on `stream`).
+ *                     The caller keeps ownership.
+ *   stream            cudaStream_t for the build.
+ *   out               receives the new graph.
+ * Synchronises `stream` (it reads sizes back to size its buffers).
+ * Returns VDMC_ERR_OUT_OF_RANGE_VERTEX if an endpoint is outside [0, n).
+ */
+vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                              int ptrs_on_device, void *stream, vdmc_graph **out);
+
+/* Free the graph's device memory (synchronises the device first). */
+vdmc_status vdmc_graph_destroy(vdmc_graph *g);
+
+/* Sizes and drop counters of a built graph (host struct, filled in). */
+vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *info);
+
+/*
+ * Copy the CSR to host buffers (a test and inspection hook).  Rows are in
+ * degree order (rank); entry = (neighbour rank << 2) | flags with flag bit 0
+ * = arc row -> neighbour and bit 1 = arc neighbour -> row; rows sorted by
+ * neighbour rank.  rowptr: int64[n+1], col: uint32[2*edges_u],
+ * new2old: int32[n] (original id of each rank).  Any pointer may be NULL.
+ * Synchronous.
+ */
+vdmc_status vdmc_graph_export_csr(const vdmc_graph *g, int64_t *rowptr, uint32_t *col,
+                                  int32_t *new2old);
+
+/* Number of output columns for k: 13 for k = 3, 199 for k = 4, -1 otherwise. */
+int vdmc_num_classes(int k);
+
+/* Minimum motif index of each output column, ascending (uint16[C_k]).
+ * Host-side table; needs no device. */
+vdmc_status vdmc_class_masks(int k, uint16_t *canon_out);
+
+/* Output column of every motif index: lut_out[idx] for idx in
+ * [0, 2^(k(k-1))), 255 where the indexed graph is not weakly connected
+ * (the isomorph merge of "The Algorithm").  Host-side table; needs no
+ * device. */
+vdmc_status vdmc_class_lut(int k, uint8_t *lut_out);
+
+/*
+ * Per-vertex counts (the VDMC algorithm of "The Algorithm"; proper k-BFS of
+ * Lemma 1; BFS structures of Lemma 2; ordering rules of Lemma 3; the
+ * direct-adjacency test of the comment after Lemma 4).
+ *   g        graph from vdmc_graph_create
+ *   k        3 or 4
+ *   out_dev  device uint64[n * C_k], row-major by ORIGINAL vertex id;
+ *            overwritten (not accumulated).  Caller owns it.
+ *   stream   cudaStream_t
+ * Asynchronous.  Calls on one graph must not overlap (they share the graph's
+ * work-queue cursor); use one graph per concurrent stream.
+ */
+vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream);
+
+/*
+ * Like vdmc_count, but only the sets whose lowest-rank member has rank in
+ * [rank_lo, rank_hi) (Lemma 1: every set has one proper root).  Disjoint
+ * ranges covering [0, n) sum to vdmc_count.  This is the unit of the
+ * root-chunk distribution of the Discussion.  Overwrites out_dev.
+ */
+vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank_hi,
+                             uint64_t *out_dev, void *stream);
+
+/*
+ * Count `num` independent graphs in ONE persistent launch (a batch of
+ * uneven small graphs; no paper counterpart).  outs[i] is a device
+ * uint64[n_i * C_k] for graphs[i], overwritten.  `graphs` and `outs` are
+ * host arrays.  Results equal num separate vdmc_count calls bit for bit.
+ * The graphs must not be used by another call until the stream reaches this
+ * point.
+ */
+vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
+                             void *stream);
+
+/* After synchronising the last stream used with g: the device status word
+ * (VDMC_OK or VDMC_ERR_DEVICE_LIMIT); reading it resets it to VDMC_OK. */
+vdmc_status vdmc_get_device_status(vdmc_graph *g);
+
+/*
+ * Measurement hook: the algorithmic byte count of one vdmc_count(g, k):
+ * 4 bytes per adjacency entry the method must read at least once per use --
+ * N(r) for every root, N(a) for every depth-1 vertex of every root and, for
+ * k = 4, N(b) for every depth-2 vertex -- plus the 8 * n * C_k bytes of the
+ * output and 4 * n bytes of the id map.  The cost model of the section on
+ * efficacy on simulated graphs: work proportional to the neighbourhoods
+ * visited.  Synchronous; runs on the legacy default stream.
+ */
+vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes);
+
+/* Global launch schedule (the autotuner's knobs).  Affects later calls. */
+vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s);
+vdmc_status vdmc_get_schedule(vdmc_schedule_t *s);
+
+/* Static description of a status code. */
+const char *vdmc_status_string(vdmc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDMC_H */

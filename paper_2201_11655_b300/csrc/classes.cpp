@@ -1,0 +1,139 @@
+// Motif class tables, built once per k on the host.
+//
+// The motif index of an ordered k-tuple is its adjacency matrix read row by
+// row with the diagonal removed, most significant bit first (Definitions,
+// Fig. 1: 110101 = 53).  Isomorphic indices are merged into the class named
+// by the minimum index (isomorph-merge paragraph of "The Algorithm"; Fig. 1:
+// 53 -> 30).
+//
+// Method used here: orbits.  S_k is generated by the adjacent transpositions
+// (i i+1); the class of an index is its orbit under the group, found by a
+// closure over those generators, and its name is the smallest member.  Only
+// weakly connected orbits (Definitions: a k-motif is connected in G_U) get
+// an output column; columns are in ascending order of the class name.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "vdmc_internal.cuh"
+
+namespace {
+
+int bit_pos(int k, int i, int j) {
+    // position of entry (i, j), i != j, counted from the least significant bit
+    int before = i * (k - 1) + (j > i ? j - 1 : j);
+    return k * (k - 1) - 1 - before;
+}
+
+int entry(int k, int idx, int i, int j) { return (idx >> bit_pos(k, i, j)) & 1; }
+
+// swap vertices t and t+1 of the matrix encoded by idx
+int swap_adjacent(int k, int idx, int t) {
+    int perm[4] = {0, 1, 2, 3};
+    perm[t] = t + 1;
+    perm[t + 1] = t;
+    int out = 0;
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < k; j++)
+            if (i != j && entry(k, idx, perm[i], perm[j])) out |= 1 << bit_pos(k, i, j);
+    return out;
+}
+
+bool weakly_connected(int k, int idx) {
+    int parent[4] = {0, 1, 2, 3};
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++)
+            if (entry(k, idx, i, j) || entry(k, idx, j, i)) parent[find(i)] = find(j);
+    for (int i = 1; i < k; i++)
+        if (find(i) != find(0)) return false;
+    return true;
+}
+
+struct Table {
+    std::vector<uint8_t> lut;
+    std::vector<uint16_t> canon;
+};
+
+Table build(int k) {
+    const int nidx = 1 << (k * (k - 1));
+    std::vector<int> name(nidx, -1);
+    std::vector<int> stack, orbit;
+    for (int start = 0; start < nidx; start++) {
+        if (name[start] >= 0) continue;
+        orbit.clear();
+        stack.assign(1, start);
+        name[start] = start;
+        while (!stack.empty()) {
+            int x = stack.back();
+            stack.pop_back();
+            orbit.push_back(x);
+            for (int t = 0; t + 1 < k; t++) {
+                int y = swap_adjacent(k, x, t);
+                if (name[y] < 0) {
+                    name[y] = start;
+                    stack.push_back(y);
+                }
+            }
+        }
+        int lo = *std::min_element(orbit.begin(), orbit.end());
+        for (int x : orbit) name[x] = lo;
+    }
+    Table T;
+    for (int idx = 0; idx < nidx; idx++)
+        if (name[idx] == idx && weakly_connected(k, idx)) T.canon.push_back((uint16_t)idx);
+    T.lut.assign(nidx, 255);
+    for (int idx = 0; idx < nidx; idx++) {
+        if (!weakly_connected(k, idx)) continue;
+        auto it = std::lower_bound(T.canon.begin(), T.canon.end(), (uint16_t)name[idx]);
+        T.lut[idx] = (uint8_t)(it - T.canon.begin());
+    }
+    return T;
+}
+
+Table g_tab[5];
+std::once_flag g_once[5];
+
+const Table *table(int k) {
+    if (k != 3 && k != 4) return nullptr;
+    std::call_once(g_once[k], [k] { g_tab[k] = build(k); });
+    return &g_tab[k];
+}
+
+}  // namespace
+
+const uint8_t *vdmc_host_lut(int k) {
+    const Table *t = table(k);
+    return t ? t->lut.data() : nullptr;
+}
+
+const uint16_t *vdmc_host_canon(int k, int *num_classes) {
+    const Table *t = table(k);
+    if (!t) return nullptr;
+    if (num_classes) *num_classes = (int)t->canon.size();
+    return t->canon.data();
+}
+
+extern "C" int vdmc_num_classes(int k) {
+    int nc = -1;
+    if (!vdmc_host_canon(k, &nc)) return -1;
+    return nc;
+}
+
+extern "C" vdmc_status vdmc_class_masks(int k, uint16_t *canon_out) {
+    int nc = 0;
+    const uint16_t *c = vdmc_host_canon(k, &nc);
+    if (!c || !canon_out) return VDMC_ERR_INVALID_ARG;
+    std::copy(c, c + nc, canon_out);
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_class_lut(int k, uint8_t *lut_out) {
+    const uint8_t *l = vdmc_host_lut(k);
+    if (!l || !lut_out) return VDMC_ERR_INVALID_ARG;
+    std::copy(l, l + ((size_t)1 << (k * (k - 1))), lut_out);
+    return VDMC_OK;
+}

@@ -1,0 +1,498 @@
+// Per-vertex directed 3/4-motif enumeration (VDMC, "The Algorithm").
+//
+// Every connected k-set S is enumerated exactly once, from its lowest-rank
+// vertex r (a proper k-BFS, Lemma 1), in exactly one BFS structure (Lemma 2)
+// taken in one member order (Lemma 3).  Depths are set-internal BFS depths
+// from r; the last vertex of a depth-3 chain is tested for direct adjacency
+// to r and to the depth-1 vertex (the fix after Lemma 4), which needs no
+// global depth marks.
+//
+// With P = N+(r) (neighbours of rank > r, sorted), the structures are
+//   k = 3  star  (depth 2/3): a < b in P
+//          path  (depth 1)  : a in P, b in N(a) \ N(r), b > r
+//   k = 4  (1,1,1) depth 0.75: a < b < c in P
+//          (1,1,2) depth 1   : a < b in P, c not in N(r), c > r, and
+//                              c in N(a), or c in N(b) \ N(a)
+//          (1,2,2) depth 1.25: a in P, b < c both in N(a) \ N(r), > r
+//          (1,2,3) depth 1.5 : a in P, b in N(a) \ N(r), b > r,
+//                              c in N(b) \ (N(r) u N(a)), c > r
+// Each set's adjacency-matrix index (Fig. 1 bit order, members r,a,b,c) is
+// mapped through the class table to an output column and every member gets
+// +1 there ("increase the counter for each vertex in the k-BFS").
+//
+// Work decomposition: one warp per task; a task is a root and an
+// interleaved slice of its depth-1 neighbours a (the paper's
+// (vertex, neighbour) pairs).  Persistent warps take tasks from a device
+// cursor with one atomicAdd; tasks are in rank order, so the heavy
+// (high-degree, low-rank) roots go first.  Credits to r, a and b, which are
+// fixed across inner loops, accumulate in per-warp shared-memory histograms
+// and are flushed with one global atomicAdd per touched column; credits to
+// the innermost member go straight to global memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "vdmc_internal.cuh"
+
+namespace {
+
+vdmc_schedule_t g_sched = {16, 8, 0, 0};
+std::mutex g_sched_mu;
+
+struct DevLut {
+    uint8_t *lut[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+DevLut g_lut[64];  // per device
+std::mutex g_lut_mu;
+
+cudaError_t device_lut(int k, const uint8_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_lut_mu);
+    if (!g_lut[dev].lut[k]) {
+        size_t bytes = (size_t)1 << (k * (k - 1));
+        uint8_t *p = nullptr;
+        e = cudaMalloc((void **)&p, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(p, vdmc_host_lut(k), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return e;
+        }
+        g_lut[dev].lut[k] = p;
+    }
+    *out = g_lut[dev].lut[k];
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------ tasks -----
+
+__global__ void task_counts(const int64_t *rowptr, const int64_t *pbeg, int32_t n, int32_t a_chunk,
+                            int64_t *cnt) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t L = rowptr[r + 1] - pbeg[r];
+    cnt[r] = L > 0 ? (L + a_chunk - 1) / a_chunk : 0;
+}
+
+__global__ void task_fill(const int64_t *rowptr, const int64_t *pbeg, const int64_t *off, int32_t n,
+                          int32_t a_chunk, Task *tasks) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t L = rowptr[r + 1] - pbeg[r];
+    if (L <= 0) return;
+    int32_t t = (int32_t)((L + a_chunk - 1) / a_chunk);
+    int64_t o = off[r];
+    for (int32_t j = 0; j < t; j++) tasks[o + j] = Task{r, j, t, 0};
+}
+
+// ------------------------------------------------------- enumeration -----
+
+struct Csr {
+    const int64_t *__restrict__ rowptr;
+    const uint32_t *__restrict__ col;
+    const int64_t *__restrict__ pbeg;
+};
+
+// flags of neighbour v in the sorted entries col[lo, hi); 0 if absent.
+// A stored edge always has non-zero flags.
+__device__ __forceinline__ uint32_t search_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
+                                               uint32_t v) {
+    const uint32_t *p = col + lo;
+    int32_t len = (int32_t)(hi - lo);
+    while (len > 0) {
+        int32_t half = len >> 1;
+        uint32_t e = __ldg(p + half);
+        if ((e >> 2) < v) {
+            p += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    if (p < col + hi) {
+        uint32_t e = __ldg(p);
+        if ((e >> 2) == v) return e & 3u;
+    }
+    return 0u;
+}
+
+// first position in col[lo, hi) with neighbour rank > v
+__device__ __forceinline__ int64_t upper_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
+                                             uint32_t v) {
+    int32_t len = (int32_t)(hi - lo);
+    int64_t base = lo;
+    while (len > 0) {
+        int32_t half = len >> 1;
+        if ((__ldg(col + base + half) >> 2) <= v) {
+            base += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return base;
+}
+
+// flags of the pair (u, v): bit0 = arc u->v, bit1 = arc v->u; 0 = no edge.
+__device__ __forceinline__ uint32_t pair_flags(const Csr &g, uint32_t u, uint32_t v) {
+    int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
+    int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
+    if (ue - ub <= ve - vb) return search_row(g.col, ub, ue, v);
+    uint32_t f = search_row(g.col, vb, ve, u);
+    return ((f & 1u) << 1) | (f >> 1);
+}
+
+// Motif index of the ordered tuple (r, a, b) from the three pair flags.
+// Bit order (Fig. 1): (0,1) (0,2) (1,0) (1,2) (2,0) (2,1), MSB first.
+__device__ __forceinline__ uint32_t mask3(uint32_t fra, uint32_t frb, uint32_t fab) {
+    return ((fra & 1u) << 5) | ((frb & 1u) << 4) | ((fra >> 1) << 3) | ((fab & 1u) << 2) | ((frb >> 1) << 1) |
+           (fab >> 1);
+}
+
+// Motif index of (r, a, b, c): (0,1) (0,2) (0,3) (1,0) (1,2) (1,3) (2,0)
+// (2,1) (2,3) (3,0) (3,1) (3,2), MSB first.
+__device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t frc, uint32_t fab, uint32_t fac,
+                                          uint32_t fbc) {
+    return ((fra & 1u) << 11) | ((frb & 1u) << 10) | ((frc & 1u) << 9) | ((fra >> 1) << 8) | ((fab & 1u) << 7) |
+           ((fac & 1u) << 6) | ((frb >> 1) << 5) | ((fab >> 1) << 4) | ((fbc & 1u) << 3) | ((frc >> 1) << 2) |
+           ((fac >> 1) << 1) | (fbc >> 1);
+}
+
+__device__ __forceinline__ void flush_hist(unsigned long long *hist, int C, uint64_t *out, int32_t orig,
+                                           int lane) {
+    __syncwarp();
+    for (int c = lane; c < C; c += 32) {
+        unsigned long long v = hist[c];
+        if (v) {
+            atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
+            hist[c] = 0ull;
+        }
+    }
+    __syncwarp();
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const GraphDesc *__restrict__ multi,
+                                                   const Task *__restrict__ tasks, int64_t ntasks,
+                                                   unsigned long long *qhead, const uint8_t *__restrict__ lut_g,
+                                                   int32_t rank_lo, int32_t rank_hi, int *status) {
+    constexpr int C = (K == 3) ? 13 : 199;
+    constexpr int NIDX = 1 << (K * (K - 1));
+    constexpr int NH = (K == 3) ? 2 : 3;  // histograms per warp: r, a (, b)
+    extern __shared__ unsigned long long smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint8_t *lut = (uint8_t *)(smem + (size_t)nwarps * NH * C);
+    unsigned long long *hist_r = smem + (size_t)warp * NH * C;
+    unsigned long long *hist_a = hist_r + C;
+    unsigned long long *hist_b = hist_r + 2 * C;  // K == 4 only
+    // A disconnected index never reaches the table by construction; should
+    // one appear, it is counted in no column and flags the status word.
+    for (int i = threadIdx.x; i < NIDX; i += blockDim.x) {
+        uint8_t v = lut_g[i];
+        lut[i] = v;
+    }
+    for (int i = threadIdx.x; i < nwarps * NH * C; i += blockDim.x) smem[i] = 0ull;
+    __syncthreads();
+
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(qhead, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)ntasks) break;
+        const Task task = tasks[t];
+        const GraphDesc &G = multi ? multi[task.g] : single;
+        const int32_t r = task.r;
+        if (r < rank_lo || r >= rank_hi) continue;
+        Csr g{G.rowptr, G.col, G.pbeg};
+        uint64_t *out = G.out;
+        const int64_t pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        const int32_t L = (int32_t)(pe - pb);
+
+        for (int32_t ia = task.j; ia < L; ia += task.stride) {
+            const uint32_t ea = __ldg(g.col + pb + ia);
+            const uint32_t a = ea >> 2, fra = ea & 3u;
+            const int64_t a_beg = __ldg(g.rowptr + a), a_end = __ldg(g.rowptr + a + 1);
+            const int64_t a_up = upper_row(g.col, a_beg, a_end, (uint32_t)r);  // N(a) with rank > r
+            if (K == 3) {
+                // star: b in P after a
+                for (int32_t ib = ia + 1 + lane; ib < L; ib += 32) {
+                    const uint32_t eb = __ldg(g.col + pb + ib);
+                    const uint32_t b = eb >> 2, frb = eb & 3u;
+                    const uint32_t cls = lut[mask3(fra, frb, pair_flags(g, a, b))];
+                    if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                    atomicAdd(&hist_r[cls], 1ull);
+                    atomicAdd(&hist_a[cls], 1ull);
+                    atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + b) * C + cls], 1ull);
+                }
+                // path: b in N(a) \ N(r), b > r
+                for (int64_t x = a_up + lane; x < a_end; x += 32) {
+                    const uint32_t eb = __ldg(g.col + x);
+                    const uint32_t b = eb >> 2;
+                    if (search_row(g.col, pb, pe, b)) continue;
+                    const uint32_t cls = lut[mask3(fra, 0u, eb & 3u)];
+                    if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                    atomicAdd(&hist_r[cls], 1ull);
+                    atomicAdd(&hist_a[cls], 1ull);
+                    atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + b) * C + cls], 1ull);
+                }
+            } else {
+                // (A1) b in P after a
+                for (int32_t ib = ia + 1; ib < L; ib++) {
+                    const uint32_t eb = __ldg(g.col + pb + ib);
+                    const uint32_t b = eb >> 2, frb = eb & 3u;
+                    const uint32_t fab = pair_flags(g, a, b);
+                    const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
+                    // (1,1,1): c in P after b
+                    for (int32_t ic = ib + 1 + lane; ic < L; ic += 32) {
+                        const uint32_t ec = __ldg(g.col + pb + ic);
+                        const uint32_t c = ec >> 2, frc = ec & 3u;
+                        const uint32_t cls = lut[mask4(fra, frb, frc, fab, pair_flags(g, a, c), pair_flags(g, b, c))];
+                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        atomicAdd(&hist_r[cls], 1ull);
+                        atomicAdd(&hist_a[cls], 1ull);
+                        atomicAdd(&hist_b[cls], 1ull);
+                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                    }
+                    // (1,1,2) with c in N(a) \ N(r), c > r
+                    for (int64_t x = a_up + lane; x < a_end; x += 32) {
+                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t c = ec >> 2;
+                        if (search_row(g.col, pb, pe, c)) continue;
+                        const uint32_t cls = lut[mask4(fra, frb, 0u, fab, ec & 3u, pair_flags(g, b, c))];
+                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        atomicAdd(&hist_r[cls], 1ull);
+                        atomicAdd(&hist_a[cls], 1ull);
+                        atomicAdd(&hist_b[cls], 1ull);
+                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                    }
+                    // (1,1,2) with c in N(b) \ N(a) \ N(r), c > r
+                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
+                    for (int64_t x = b_up + lane; x < b_end; x += 32) {
+                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t c = ec >> 2;
+                        if (search_row(g.col, pb, pe, c)) continue;
+                        if (pair_flags(g, a, c)) continue;
+                        const uint32_t cls = lut[mask4(fra, frb, 0u, fab, 0u, ec & 3u)];
+                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        atomicAdd(&hist_r[cls], 1ull);
+                        atomicAdd(&hist_a[cls], 1ull);
+                        atomicAdd(&hist_b[cls], 1ull);
+                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                    }
+                    flush_hist(hist_b, C, out, __ldg(G.new2old + b), lane);
+                }
+                // (A2) b in N(a) \ N(r), b > r
+                for (int64_t xb = a_up; xb < a_end; xb++) {
+                    const uint32_t eb = __ldg(g.col + xb);
+                    const uint32_t b = eb >> 2, fab = eb & 3u;
+                    if (search_row(g.col, pb, pe, b)) continue;  // warp-uniform
+                    const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
+                    // (1,2,2): c in N(a) after b, c not in N(r)
+                    for (int64_t x = xb + 1 + lane; x < a_end; x += 32) {
+                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t c = ec >> 2;
+                        if (search_row(g.col, pb, pe, c)) continue;
+                        const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, ec & 3u, pair_flags(g, b, c))];
+                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        atomicAdd(&hist_r[cls], 1ull);
+                        atomicAdd(&hist_a[cls], 1ull);
+                        atomicAdd(&hist_b[cls], 1ull);
+                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                    }
+                    // (1,2,3): c in N(b), c > r, not in N(r), not adjacent to a
+                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
+                    for (int64_t x = b_up + lane; x < b_end; x += 32) {
+                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t c = ec >> 2;
+                        if (search_row(g.col, pb, pe, c)) continue;
+                        if (pair_flags(g, a, c)) continue;
+                        const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, 0u, ec & 3u)];
+                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        atomicAdd(&hist_r[cls], 1ull);
+                        atomicAdd(&hist_a[cls], 1ull);
+                        atomicAdd(&hist_b[cls], 1ull);
+                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                    }
+                    flush_hist(hist_b, C, out, __ldg(G.new2old + b), lane);
+                }
+            }
+            flush_hist(hist_a, C, out, __ldg(G.new2old + a), lane);
+        }
+        flush_hist(hist_r, C, out, __ldg(G.new2old + r), lane);
+    }
+}
+
+// Algorithmic bytes of one count: the adjacency lists the method must read
+// at least once per use (N(r) per root, N(a) per depth-1 vertex a and, for
+// k = 4, N(b) per depth-2 vertex b), 4 bytes per entry.
+__global__ void work_bytes_kernel(Csr g, int32_t n, int k, unsigned long long *total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (int64_t r = wid; r < n; r += nw) {
+        const int64_t rb = __ldg(g.rowptr + r), pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        if (lane == 0) acc += (unsigned long long)(pe - rb);
+        for (int64_t x = pb + lane; x < pe; x += 32) {
+            const uint32_t a = __ldg(g.col + x) >> 2;
+            const int64_t ab = __ldg(g.rowptr + a), ae = __ldg(g.rowptr + a + 1);
+            acc += (unsigned long long)(ae - ab);
+            if (k == 4) {
+                for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r); y < ae; y++) {
+                    const uint32_t b = __ldg(g.col + y) >> 2;
+                    if (search_row(g.col, pb, pe, b)) continue;
+                    acc += (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0 && acc) atomicAdd(total, acc * 4ull);
+}
+
+size_t smem_bytes(int k, int warps) {
+    int C = k == 3 ? 13 : 199, NH = k == 3 ? 2 : 3;
+    return (size_t)warps * NH * C * sizeof(unsigned long long) + ((size_t)1 << (k * (k - 1)));
+}
+
+vdmc_status launch_count(int k, const GraphDesc &single, const GraphDesc *multi, const Task *tasks,
+                         int64_t ntasks, unsigned long long *qhead, int32_t lo, int32_t hi, int *status,
+                         cudaStream_t s) {
+    const uint8_t *lut = nullptr;
+    VDMC_CUDA_TRY(device_lut(k, &lut));
+    vdmc_schedule_t sch;
+    vdmc_current_schedule(&sch);
+    int warps = std::max(1, std::min(8, sch.warps_per_block));
+    int threads = warps * 32;
+    size_t smem = smem_bytes(k, warps);
+    int dev = 0, sms = 0;
+    VDMC_CUDA_TRY(cudaGetDevice(&dev));
+    VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kern = (k == 3) ? count_kernel<3> : count_kernel<4>;
+    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (sch.blocks_per_sm > 0) per_sm = std::min(per_sm, sch.blocks_per_sm);
+    int64_t grid = (int64_t)sms * per_sm;
+    int64_t need = (ntasks + warps - 1) / warps;
+    if (grid > need) grid = std::max<int64_t>(1, need);
+    VDMC_CUDA_TRY(cudaMemsetAsync(qhead, 0, sizeof(unsigned long long), s));
+    if (ntasks > 0) {
+        kern<<<(unsigned)grid, threads, smem, s>>>(single, multi, tasks, ntasks, qhead, lut, lo, hi, status);
+        VDMC_CUDA_TRY(cudaGetLastError());
+    }
+    return VDMC_OK;
+}
+
+}  // namespace
+
+void vdmc_current_schedule(vdmc_schedule_t *s) {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    *s = g_sched;
+}
+
+vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s) {
+    if (a_chunk < 1) return VDMC_ERR_INVALID_ARG;
+    cudaFree(g->tasks);
+    g->tasks = nullptr;
+    g->ntasks = 0;
+    const int32_t n = g->n;
+    int64_t *cnt = nullptr;
+    VDMC_CUDA_TRY(cudaMallocAsync((void **)&cnt, sizeof(int64_t) * ((size_t)n + 1), s));
+    if (n > 0) {
+        task_counts<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, n, a_chunk, cnt);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = vdmc_exclusive_scan_i64(cnt, cnt, n, s);
+    int64_t total = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cnt + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->tasks, sizeof(Task) * (size_t)(total ? total : 1));
+    if (e == cudaSuccess && n > 0) {
+        task_fill<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, cnt, n, a_chunk, g->tasks);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(cnt, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
+    g->ntasks = total;
+    g->tasks_a_chunk = a_chunk;
+    return VDMC_OK;
+}
+
+static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s) {
+    if (!g || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
+    if (!out && g->n > 0) return VDMC_ERR_INVALID_ARG;
+    const int C = k == 3 ? 13 : 199;
+    vdmc_schedule_t sch;
+    vdmc_current_schedule(&sch);
+    if (g->tasks_a_chunk != sch.a_chunk) {
+        vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, s);
+        if (st != VDMC_OK) return st;
+    }
+    if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
+    GraphDesc d{g->rowptr, g->col, g->pbeg, g->new2old, out, g->n, 0};
+    return launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
+}
+
+extern "C" vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {
+    return count_impl(g, k, 0, g ? g->n : 0, out_dev, (cudaStream_t)stream);
+}
+
+extern "C" vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank_hi, uint64_t *out_dev,
+                                        void *stream) {
+    if (!g || rank_lo < 0 || rank_hi < rank_lo) return VDMC_ERR_INVALID_ARG;
+    return count_impl(g, k, rank_lo, std::min(rank_hi, g->n), out_dev, (cudaStream_t)stream);
+}
+
+extern "C" vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
+                                        void *stream) {
+    // First version: one launch per graph on the same stream.
+    if (num < 0 || (num > 0 && (!graphs || !outs))) return VDMC_ERR_INVALID_ARG;
+    for (int i = 0; i < num; i++) {
+        vdmc_status st = vdmc_count(graphs[i], k, outs[i], stream);
+        if (st != VDMC_OK) return st;
+    }
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes) {
+    if (!g || !bytes || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
+    unsigned long long *d = nullptr;
+    VDMC_CUDA_TRY(cudaMalloc((void **)&d, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess && g->n > 0) {
+        Csr c{g->rowptr, g->col, g->pbeg};
+        work_bytes_kernel<<<1184, 256>>>(c, g->n, k, d);
+        e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return VDMC_ERR_CUDA;
+    const int C = k == 3 ? 13 : 199;
+    *bytes = (uint64_t)h + 8ull * (uint64_t)g->n * (uint64_t)C + 4ull * (uint64_t)g->n;
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s) {
+    if (!s || s->a_chunk < 1 || s->warps_per_block < 1 || s->warps_per_block > 8 || s->blocks_per_sm < 0)
+        return VDMC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched = *s;
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_get_schedule(vdmc_schedule_t *s) {
+    if (!s) return VDMC_ERR_INVALID_ARG;
+    vdmc_current_schedule(s);
+    return VDMC_OK;
+}

@@ -1,0 +1,81 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "vdmc.h"
+
+#define VDMC_MAX_CLASSES 199
+
+// One unit of enumeration work: root rank r, and the slice of its depth-1
+// neighbours it owns: positions j, j + stride, j + 2*stride, ... of N+(r).
+// (The paper computes each (vertex, neighbour) pair separately on the GPU,
+// "Vertex ordering and splitting over the GPU"; a slice groups such pairs.)
+struct Task {
+    int32_t r;
+    int32_t j;
+    int32_t stride;
+    int32_t g;       // graph index inside a batch launch
+};
+
+// Read-only view of one graph's device CSR plus the output it writes.
+struct GraphDesc {
+    const int64_t *rowptr;   // [n+1]
+    const uint32_t *col;     // [2E_U]  (rank << 2) | flags
+    const int64_t *pbeg;     // [n]  first entry of row r with rank > r
+    const int32_t *new2old;  // [n]
+    uint64_t *out;           // [n * C_k], original-id rows
+    int32_t n;
+    int32_t pad;
+};
+
+struct vdmc_graph {
+    int device;
+    int32_t n;
+    int64_t nnz;             // 2 * E_U
+    int64_t *rowptr;
+    uint32_t *col;
+    int64_t *pbeg;
+    int32_t *new2old;
+    int32_t *old2new;
+    Task *tasks;
+    int64_t ntasks;
+    int32_t tasks_a_chunk;
+    unsigned long long *qhead;   // work-queue cursor
+    int *status;                 // device status word
+    vdmc_graph_info_t info;
+};
+
+// ---- status helpers ----
+#define VDMC_CUDA_TRY(expr)                                         \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) {                                    \
+            return (_e == cudaErrorMemoryAllocation) ? VDMC_ERR_OOM \
+                                                     : VDMC_ERR_CUDA; \
+        }                                                           \
+    } while (0)
+
+// ---- primitives (sort_scan.cu) ----
+// Exclusive prefix sum in place-or-not: out[i] = sum_{j<i} in[i]; out[count] = total
+// when `out` has count+1 slots (total_slot != 0).  Temporary storage comes
+// from the stream-ordered allocator.
+cudaError_t vdmc_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t count, cudaStream_t s);
+cudaError_t vdmc_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t count, cudaStream_t s);
+// LSD radix sort of 64-bit keys on bits [begin_bit, end_bit); the other bits
+// ride along.  Stable.  On return *result points at whichever of keys / tmp
+// holds the sorted keys.
+cudaError_t vdmc_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t count, int begin_bit,
+                                int end_bit, cudaStream_t s, uint64_t **result);
+
+// ---- classes (classes.cpp) ----
+// lut[mask] = output column of the motif with index `mask`, 255 if the
+// induced graph is not weakly connected.  Built once per k, host memory.
+const uint8_t *vdmc_host_lut(int k);
+const uint16_t *vdmc_host_canon(int k, int *num_classes);
+
+// ---- schedule / tasks (count.cu) ----
+vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s);
+void vdmc_current_schedule(vdmc_schedule_t *s);

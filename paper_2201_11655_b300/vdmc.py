@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in ``include/vdmc.h`` (argument marshalling only).
+
+Every step of the counting runs in ``libvdmc.so``; this module converts torch
+tensors / numpy arrays into pointers, sizes and a ``cudaStream_t`` and
+checks status codes.  There is no CPU fallback: if the library or a CUDA
+device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvdmc.so")
+
+VDMC_OK = 0
+STATUS_NAMES = {
+    0: "VDMC_OK", 1: "VDMC_ERR_INVALID_ARG", 2: "VDMC_ERR_OUT_OF_RANGE_VERTEX", 3: "VDMC_ERR_OOM",
+    4: "VDMC_ERR_CUDA", 5: "VDMC_ERR_DEVICE_LIMIT", 6: "VDMC_ERR_BUSY",
+}
+
+
+class VdmcError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        msg = _lib().vdmc_status_string(int(status)).decode() if _LIB is not None else str(status)
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(int(status), status), msg))
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("arcs_in", ctypes.c_int64),
+        ("self_loops", ctypes.c_int64), ("duplicate_arcs", ctypes.c_int64), ("arcs_kept", ctypes.c_int64),
+        ("edges_u", ctypes.c_int64), ("reciprocal_pairs", ctypes.c_int64), ("num_tasks", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("a_chunk", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libvdmc.so not built (%s); run paper_2201_11655_b300.build" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "vdmc_graph_create": ([i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+            "vdmc_graph_destroy": ([vp], ctypes.c_int),
+            "vdmc_graph_info": ([vp, ctypes.POINTER(GraphInfo)], ctypes.c_int),
+            "vdmc_graph_export_csr": ([vp, vp, vp, vp], ctypes.c_int),
+            "vdmc_num_classes": ([ctypes.c_int], ctypes.c_int),
+            "vdmc_class_masks": ([ctypes.c_int, vp], ctypes.c_int),
+            "vdmc_class_lut": ([ctypes.c_int, vp], ctypes.c_int),
+            "vdmc_count": ([vp, ctypes.c_int, vp, vp], ctypes.c_int),
+            "vdmc_count_roots": ([vp, ctypes.c_int, i32, i32, vp, vp], ctypes.c_int),
+            "vdmc_count_batch": ([vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+            "vdmc_get_device_status": ([vp], ctypes.c_int),
+            "vdmc_work_bytes": ([vp, ctypes.c_int, vp], ctypes.c_int),
+            "vdmc_set_schedule": ([ctypes.POINTER(Schedule)], ctypes.c_int),
+            "vdmc_get_schedule": ([ctypes.POINTER(Schedule)], ctypes.c_int),
+            "vdmc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load libvdmc.so (raises if it is missing) and return the ctypes handle."""
+    return _lib()
+
+
+def _check(st, where):
+    if st != VDMC_OK:
+        raise VdmcError(st, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def num_classes(k: int) -> int:
+    return _lib().vdmc_num_classes(k)
+
+
+def class_masks(k: int) -> np.ndarray:
+    nc = num_classes(k)
+    if nc < 0:
+        raise ValueError("k must be 3 or 4")
+    out = np.zeros(nc, np.uint16)
+    _check(_lib().vdmc_class_masks(k, out.ctypes.data), "vdmc_class_masks")
+    return out
+
+
+def class_lut(k: int) -> np.ndarray:
+    """Output column of every motif index (255 = not weakly connected)."""
+    if k not in (3, 4):
+        raise ValueError("k must be 3 or 4")
+    out = np.zeros(1 << (k * (k - 1)), np.uint8)
+    _check(_lib().vdmc_class_lut(k, out.ctypes.data), "vdmc_class_lut")
+    return out
+
+
+class Graph:
+    """A device graph built by ``vdmc_graph_create``; freed by ``close()``."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph is closed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = GraphInfo()
+        _check(_lib().vdmc_graph_info(self.handle, ctypes.byref(inf)), "vdmc_graph_info")
+        return inf.as_dict()
+
+    def export_csr(self):
+        info = self.info()
+        rowptr = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(2 * info["edges_u"], np.uint32)
+        new2old = np.zeros(self.n, np.int32)
+        _check(_lib().vdmc_graph_export_csr(self.handle, rowptr.ctypes.data, col.ctypes.data,
+                                            new2old.ctypes.data), "vdmc_graph_export_csr")
+        return rowptr, col, new2old
+
+    def work_bytes(self, k: int) -> int:
+        """Algorithmic bytes of one count (the roofline numerator)."""
+        b = np.zeros(1, np.uint64)
+        _check(_lib().vdmc_work_bytes(self.handle, int(k), b.ctypes.data), "vdmc_work_bytes")
+        return int(b[0])
+
+    def device_status(self) -> int:
+        return _lib().vdmc_get_device_status(self.handle)
+
+    def close(self):
+        if self._h is not None:
+            _check(_lib().vdmc_graph_destroy(self._h), "vdmc_graph_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def graph_create(n: int, src, dst, stream=None) -> Graph:
+    """Build a graph from arcs src[e] -> dst[e] (int32; numpy/CPU tensors or CUDA tensors)."""
+    import torch
+    lib = _lib()
+    on_device = 0
+    keep = []
+    if isinstance(src, torch.Tensor) and src.is_cuda:
+        s = src.to(torch.int32).contiguous()
+        d = dst.to(device=s.device, dtype=torch.int32).contiguous()
+        on_device = 1
+        keep += [s, d]
+        ps, pd, m = s.data_ptr(), d.data_ptr(), s.numel()
+    else:
+        s = np.ascontiguousarray(np.asarray(src.cpu() if isinstance(src, torch.Tensor) else src, dtype=np.int32))
+        d = np.ascontiguousarray(np.asarray(dst.cpu() if isinstance(dst, torch.Tensor) else dst, dtype=np.int32))
+        keep += [s, d]
+        ps, pd, m = s.ctypes.data, d.ctypes.data, s.size
+    if (d.numel() if on_device else d.size) != m:
+        raise ValueError("src and dst differ in length")
+    h = ctypes.c_void_p()
+    _check(lib.vdmc_graph_create(int(n), int(m), ctypes.c_void_p(ps), ctypes.c_void_p(pd), on_device,
+                                 _stream_ptr(stream), ctypes.byref(h)), "vdmc_graph_create")
+    return Graph(h, int(n))
+
+
+def _out_tensor(g: Graph, k: int, out):
+    import torch
+    nc = num_classes(k)
+    if nc < 0:
+        raise ValueError("k must be 3 or 4")
+    if out is None:
+        out = torch.empty((g.n, nc), dtype=torch.uint64, device="cuda")
+    if out.dtype != torch.uint64 or not out.is_cuda or out.numel() != g.n * nc or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA uint64 tensor of n*C_k elements")
+    return out
+
+
+def count(g: Graph, k: int, out=None, stream=None):
+    """Per-vertex counts, uint64[n, C_k] CUDA tensor (overwritten)."""
+    out = _out_tensor(g, k, out)
+    _check(_lib().vdmc_count(g.handle, int(k), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "vdmc_count")
+    return out
+
+
+def count_roots(g: Graph, k: int, rank_lo: int, rank_hi: int, out=None, stream=None):
+    """Counts of the sets whose lowest-rank member has rank in [rank_lo, rank_hi)."""
+    out = _out_tensor(g, k, out)
+    _check(_lib().vdmc_count_roots(g.handle, int(k), int(rank_lo), int(rank_hi), ctypes.c_void_p(out.data_ptr()),
+                                   _stream_ptr(stream)), "vdmc_count_roots")
+    return out
+
+
+def count_batch(graphs, k: int, outs=None, stream=None):
+    """Count many graphs in one launch; returns the list of output tensors."""
+    outs = [_out_tensor(g, k, None if outs is None else outs[i]) for i, g in enumerate(graphs)]
+    num = len(graphs)
+    harr = (ctypes.c_void_p * max(num, 1))(*[g.handle for g in graphs])
+    oarr = (ctypes.c_void_p * max(num, 1))(*[o.data_ptr() for o in outs])
+    _check(_lib().vdmc_count_batch(harr, num, int(k), oarr, _stream_ptr(stream)), "vdmc_count_batch")
+    return outs
+
+
+def set_schedule(a_chunk=None, warps_per_block=None, blocks_per_sm=None):
+    cur = get_schedule()
+    s = Schedule(a_chunk if a_chunk is not None else cur["a_chunk"],
+                 warps_per_block if warps_per_block is not None else cur["warps_per_block"],
+                 blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"], 0)
+    _check(_lib().vdmc_set_schedule(ctypes.byref(s)), "vdmc_set_schedule")
+
+
+def get_schedule() -> dict:
+    s = Schedule()
+    _check(_lib().vdmc_get_schedule(ctypes.byref(s)), "vdmc_get_schedule")
+    return {"a_chunk": s.a_chunk, "warps_per_block": s.warps_per_block, "blocks_per_sm": s.blocks_per_sm}

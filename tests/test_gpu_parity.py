@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every comparison is element by element and bit-exact (uint64 counts; the
+output is a unique integer array, so the tolerance is zero).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from gpu_util import gpu_count, gpu_count_roots, to_numpy_u64
+from oracle import oracle as O
+from paper_2201_11655_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_11655_b300 import build, vdmc
+    build.build()
+    vdmc.load()
+    torch.cuda.init()
+
+
+def _arcs(pairs):
+    pairs = list(pairs)
+    return (np.array([p[0] for p in pairs], np.int32).reshape(-1),
+            np.array([p[1] for p in pairs], np.int32).reshape(-1))
+
+
+def check(n, s, d, ks=(3, 4)):
+    for k in ks:
+        want, _ = O.count(n, s, d, k)
+        got = gpu_count(n, s, d, k)
+        np.testing.assert_array_equal(got, want, err_msg="k=%d n=%d m=%d" % (k, n, len(s)))
+
+
+# ------------------------------------------------------------ graph build --
+
+def test_csr_example_build():
+    from paper_2201_11655_b300 import vdmc
+    g = read_golden("csr_example.txt")
+    arcs = [tuple(int(x) for x in a.split(">")) for a in g["arcs"]]
+    s, d = _arcs(arcs)
+    with vdmc.graph_create(4, s, d) as G:
+        info = G.info()
+        rowptr, col, new2old = G.export_csr()
+    ui = [int(x) for x in g["undirected_indices"]]
+    un = [int(x) for x in g["undirected_neighbors"]]
+    di = [int(x) for x in g["directed_indices"]]
+    dn = [int(x) for x in g["directed_neighbors"]]
+    assert info["edges_u"] == len(un) // 2 and info["arcs_kept"] == len(dn)
+    assert info["reciprocal_pairs"] == 1
+    # back to original ids: undirected neighbour sets and directed out-lists
+    und = {v: set() for v in range(4)}
+    out = {v: set() for v in range(4)}
+    for r in range(4):
+        v = int(new2old[r])
+        for e in col[rowptr[r]:rowptr[r + 1]]:
+            u = int(new2old[int(e) >> 2])
+            und[v].add(u)
+            if e & 1:
+                out[v].add(u)
+    for v in range(4):
+        assert sorted(und[v]) == un[ui[v]:ui[v + 1]]
+        assert sorted(out[v]) == dn[di[v]:di[v + 1]]
+    # rows in rank order are sorted; ranks follow degree descending, id ascending
+    deg = np.diff(ui)
+    order = np.lexsort((np.arange(4), -deg))
+    np.testing.assert_array_equal(new2old, order)
+
+
+def test_build_counters_and_drops():
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.gnp(50, 0.1, 3)
+    s2 = np.concatenate([s, s[:17], [4, 9, 9]]).astype(np.int32)
+    d2 = np.concatenate([d, d[:17], [4, 9, 9]]).astype(np.int32)
+    with vdmc.graph_create(n, s2, d2) as G:
+        info = G.info()
+    assert info["self_loops"] == 3 and info["duplicate_arcs"] == 17
+    assert info["arcs_kept"] == len(s)
+    pairs = set(zip(s.tolist(), d.tolist()))
+    und = {(min(a, b), max(a, b)) for a, b in pairs}
+    assert info["edges_u"] == len(und)
+    assert info["reciprocal_pairs"] == sum(1 for a, b in pairs if (b, a) in pairs) // 2
+
+
+def test_build_from_device_pointers():
+    n, s, d = synth.chung_lu(500, 3.0, 2.3, 4, reciprocity=0.2)
+    want, _ = O.count(n, s, d, 3)
+    got = gpu_count(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), 3)
+    np.testing.assert_array_equal(got, want)
+
+
+# ----------------------------------------------------------- hand-worked --
+
+def test_gnp100_full_parity():
+    n, s, d = synth.gnp(100, 0.08, 0)
+    check(n, s, d)
+
+
+@pytest.mark.parametrize("n", [4, 5, 9])
+def test_complete_digraph(n):
+    s, d = _arcs((i, j) for i in range(n) for j in range(n) if i != j)
+    check(n, s, d)
+    got = gpu_count(n, s, d, 4)
+    assert (got[:, 198] == math.comb(n - 1, 3)).all()
+
+
+def test_cycles_stars_tournament():
+    for n in (3, 4, 5, 11):
+        s, d = _arcs((i, (i + 1) % n) for i in range(n))
+        check(n, s, d)
+    for L in (2, 3, 40):
+        s, d = _arcs((0, i) for i in range(1, L + 1))
+        check(L + 1, s, d)
+        check(L + 1, d, s)
+    s, d = _arcs((i, j) for i in range(7) for j in range(i + 1, 7))
+    check(7, s, d)
+
+
+# ----------------------------------------------------------- random cases --
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 300))
+    if seed % 2:
+        n, s, d = synth.gnp(n, float(rng.uniform(0.01, 0.3)), seed)
+    else:
+        n, s, d = synth.chung_lu(n, float(rng.uniform(1.0, 6.0)), float(rng.uniform(2.1, 2.8)), seed,
+                                 reciprocity=float(rng.uniform(0, 0.5)))
+    check(n, s, d)
+
+
+def test_medium_powerlaw_many_tiles():
+    # hubs of a few hundred neighbours: several warps' worth of tasks per root,
+    # ragged tails in every inner loop
+    n, s, d = synth.chung_lu(3000, 4.0, 2.2, 17, reciprocity=0.2)
+    check(n, s, d)
+
+
+def test_schedules_do_not_change_results():
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.chung_lu(1500, 4.0, 2.3, 5, reciprocity=0.2)
+    want = {k: O.count(n, s, d, k)[0] for k in (3, 4)}
+    old = vdmc.get_schedule()
+    try:
+        for a_chunk, warps, bps in ((1, 8, 0), (7, 4, 1), (64, 1, 0), (1000, 2, 3)):
+            vdmc.set_schedule(a_chunk=a_chunk, warps_per_block=warps, blocks_per_sm=bps)
+            for k in (3, 4):
+                np.testing.assert_array_equal(gpu_count(n, s, d, k), want[k])
+    finally:
+        vdmc.set_schedule(**old)
+
+
+# ---------------------------------------------------------------- edges --
+
+def test_empty_and_degenerate():
+    from paper_2201_11655_b300 import vdmc
+    e = np.zeros(0, np.int32)
+    for n in (0, 1, 6):
+        for k in (3, 4):
+            got = gpu_count(n, e, e, k)
+            assert got.shape == (n, vdmc.num_classes(k)) and not got.any()
+    # only self-loops
+    s = np.arange(5, dtype=np.int32)
+    assert not gpu_count(5, s, s, 4).any()
+    # a single arc: no 3-set is connected
+    assert not gpu_count(2, np.array([0], np.int32), np.array([1], np.int32), 3).any()
+    # fewer vertices than k
+    check(3, *_arcs([(0, 1), (1, 2), (2, 0)]), ks=(4,))
+
+
+def test_errors():
+    from paper_2201_11655_b300 import vdmc
+    with pytest.raises(vdmc.VdmcError) as ei:
+        vdmc.graph_create(5, np.array([0, 5], np.int32), np.array([1, 2], np.int32))
+    assert ei.value.status == 2
+    with pytest.raises(vdmc.VdmcError) as ei:
+        vdmc.graph_create(5, np.array([0, -1], np.int32), np.array([1, 2], np.int32))
+    assert ei.value.status == 2
+    n, s, d = synth.gnp(10, 0.3, 1)
+    with vdmc.graph_create(n, s, d) as g:
+        with pytest.raises(ValueError):
+            vdmc.count(g, 5)
+        import ctypes
+        out = torch.zeros(n * 13, dtype=torch.uint64, device="cuda")
+        st = vdmc.load().vdmc_count(g.handle, 5, ctypes.c_void_p(out.data_ptr()), None)
+        assert st == 1
+
+
+# ------------------------------------------------------------ root ranges --
+
+def test_root_ranges_partition_and_match_oracle():
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.chung_lu(2000, 4.0, 2.3, 23, reciprocity=0.2)
+    rank = O.degree_rank(n, s, d)
+    with vdmc.graph_create(n, s, d) as g:
+        _, _, new2old = g.export_csr()
+        np.testing.assert_array_equal(rank[new2old], np.arange(n))
+        for k in (3, 4):
+            acc = np.zeros((n, vdmc.num_classes(k)), np.uint64)
+            for lo, hi in ((0, 1), (1, 17), (17, 400), (400, n)):
+                part = gpu_count_roots(g, k, lo, hi)
+                want, _ = O.count_roots(n, s, d, k, rank, lo, hi)
+                np.testing.assert_array_equal(part, want)
+                acc += part
+            full = to_numpy_u64(vdmc.count(g, k))
+            np.testing.assert_array_equal(acc, full)
+
+
+def test_repeated_calls_overwrite():
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.gnp(120, 0.06, 9)
+    want, _ = O.count(n, s, d, 4)
+    with vdmc.graph_create(n, s, d) as g:
+        out = torch.full((n, 199), 7, dtype=torch.uint64, device="cuda")
+        for _ in range(3):
+            vdmc.count(g, 4, out=out)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(to_numpy_u64(out), want)
