@@ -98,7 +98,18 @@ struct Csr {
     const int64_t *__restrict__ rowptr;
     const uint32_t *__restrict__ col;
     const int64_t *__restrict__ pbeg;
+    int64_t n;
+    int64_t nnz;
+    int *status;  // device status word; also receives bounds violations
 };
+
+// Every data-dependent index is checked before use.  A violation (which a
+// correct CSR never produces) sets the status word and the access is
+// skipped, so a corrupted input cannot make the kernel fault.
+__device__ __forceinline__ bool in_bounds(const Csr &g, bool ok) {
+    if (!ok) atomicExch(g.status, (int)VDMC_ERR_DEVICE_LIMIT);
+    return ok;
+}
 
 // flags of neighbour v in the sorted entries col[lo, hi); 0 if absent.
 // A stored edge always has non-zero flags.
@@ -142,8 +153,10 @@ __device__ __forceinline__ int64_t upper_row(const uint32_t *__restrict__ col, i
 
 // flags of the pair (u, v): bit0 = arc u->v, bit1 = arc v->u; 0 = no edge.
 __device__ __forceinline__ uint32_t pair_flags(const Csr &g, uint32_t u, uint32_t v) {
+    if (!in_bounds(g, u < g.n && v < g.n)) return 0u;
     int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
     int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
+    if (!in_bounds(g, ub >= 0 && ub <= ue && ue <= g.nnz && vb >= 0 && vb <= ve && ve <= g.nnz)) return 0u;
     if (ue - ub <= ve - vb) return search_row(g.col, ub, ue, v);
     uint32_t f = search_row(g.col, vb, ve, u);
     return ((f & 1u) << 1) | (f >> 1);
@@ -165,9 +178,23 @@ __device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t f
            ((fac >> 1) << 1) | (fbc >> 1);
 }
 
-__device__ __forceinline__ void flush_hist(unsigned long long *hist, int C, uint64_t *out, int32_t orig,
-                                           int lane) {
+// +1 for vertex (rank) v in column cls of its original-id row
+__device__ __forceinline__ void credit(const Csr &g, uint64_t *out, const int32_t *new2old, uint32_t v, int C,
+                                       uint32_t cls) {
+    if (!in_bounds(g, v < g.n)) return;
+    const int32_t o = __ldg(new2old + v);
+    if (!in_bounds(g, o >= 0 && o < g.n)) return;
+    atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], 1ull);
+}
+
+__device__ __forceinline__ void flush_hist(const Csr &g, unsigned long long *hist, int C, uint64_t *out,
+                                           int32_t orig, int lane) {
     __syncwarp();
+    if (!in_bounds(g, orig >= 0 && orig < g.n)) {
+        for (int c = lane; c < C; c += 32) hist[c] = 0ull;
+        __syncwarp();
+        return;
+    }
     for (int c = lane; c < C; c += 32) {
         unsigned long long v = hist[c];
         if (v) {
@@ -208,18 +235,22 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= (unsigned long long)ntasks) break;
         const Task task = tasks[t];
-        const GraphDesc &G = multi ? multi[task.g] : single;
+        const GraphDesc G = multi ? multi[task.g] : single;
         const int32_t r = task.r;
         if (r < rank_lo || r >= rank_hi) continue;
-        Csr g{G.rowptr, G.col, G.pbeg};
+        Csr g{G.rowptr, G.col, G.pbeg, G.n, G.nnz, status};
         uint64_t *out = G.out;
+        if (!in_bounds(g, r >= 0 && r < G.n && task.stride >= 1 && task.j >= 0)) continue;
         const int64_t pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        if (!in_bounds(g, pb >= 0 && pb <= pe && pe <= G.nnz)) continue;
         const int32_t L = (int32_t)(pe - pb);
 
         for (int32_t ia = task.j; ia < L; ia += task.stride) {
             const uint32_t ea = __ldg(g.col + pb + ia);
             const uint32_t a = ea >> 2, fra = ea & 3u;
+            if (!in_bounds(g, a < G.n)) break;
             const int64_t a_beg = __ldg(g.rowptr + a), a_end = __ldg(g.rowptr + a + 1);
+            if (!in_bounds(g, a_beg >= 0 && a_beg <= a_end && a_end <= G.nnz)) break;
             const int64_t a_up = upper_row(g.col, a_beg, a_end, (uint32_t)r);  // N(a) with rank > r
             if (K == 3) {
                 // star: b in P after a
@@ -227,10 +258,10 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                     const uint32_t eb = __ldg(g.col + pb + ib);
                     const uint32_t b = eb >> 2, frb = eb & 3u;
                     const uint32_t cls = lut[mask3(fra, frb, pair_flags(g, a, b))];
-                    if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                    if (!in_bounds(g, cls < (uint32_t)C)) continue;
                     atomicAdd(&hist_r[cls], 1ull);
                     atomicAdd(&hist_a[cls], 1ull);
-                    atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + b) * C + cls], 1ull);
+                    credit(g, out, G.new2old, b, C, cls);
                 }
                 // path: b in N(a) \ N(r), b > r
                 for (int64_t x = a_up + lane; x < a_end; x += 32) {
@@ -238,28 +269,30 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                     const uint32_t b = eb >> 2;
                     if (search_row(g.col, pb, pe, b)) continue;
                     const uint32_t cls = lut[mask3(fra, 0u, eb & 3u)];
-                    if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                    if (!in_bounds(g, cls < (uint32_t)C)) continue;
                     atomicAdd(&hist_r[cls], 1ull);
                     atomicAdd(&hist_a[cls], 1ull);
-                    atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + b) * C + cls], 1ull);
+                    credit(g, out, G.new2old, b, C, cls);
                 }
             } else {
                 // (A1) b in P after a
                 for (int32_t ib = ia + 1; ib < L; ib++) {
                     const uint32_t eb = __ldg(g.col + pb + ib);
                     const uint32_t b = eb >> 2, frb = eb & 3u;
+                    if (!in_bounds(g, b < G.n)) break;
                     const uint32_t fab = pair_flags(g, a, b);
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
+                    if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
                     // (1,1,1): c in P after b
                     for (int32_t ic = ib + 1 + lane; ic < L; ic += 32) {
                         const uint32_t ec = __ldg(g.col + pb + ic);
                         const uint32_t c = ec >> 2, frc = ec & 3u;
                         const uint32_t cls = lut[mask4(fra, frb, frc, fab, pair_flags(g, a, c), pair_flags(g, b, c))];
-                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        if (!in_bounds(g, cls < (uint32_t)C)) continue;
                         atomicAdd(&hist_r[cls], 1ull);
                         atomicAdd(&hist_a[cls], 1ull);
                         atomicAdd(&hist_b[cls], 1ull);
-                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                        credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,1,2) with c in N(a) \ N(r), c > r
                     for (int64_t x = a_up + lane; x < a_end; x += 32) {
@@ -267,11 +300,11 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         const uint32_t c = ec >> 2;
                         if (search_row(g.col, pb, pe, c)) continue;
                         const uint32_t cls = lut[mask4(fra, frb, 0u, fab, ec & 3u, pair_flags(g, b, c))];
-                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        if (!in_bounds(g, cls < (uint32_t)C)) continue;
                         atomicAdd(&hist_r[cls], 1ull);
                         atomicAdd(&hist_a[cls], 1ull);
                         atomicAdd(&hist_b[cls], 1ull);
-                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                        credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,1,2) with c in N(b) \ N(a) \ N(r), c > r
                     const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
@@ -281,31 +314,33 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (search_row(g.col, pb, pe, c)) continue;
                         if (pair_flags(g, a, c)) continue;
                         const uint32_t cls = lut[mask4(fra, frb, 0u, fab, 0u, ec & 3u)];
-                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        if (!in_bounds(g, cls < (uint32_t)C)) continue;
                         atomicAdd(&hist_r[cls], 1ull);
                         atomicAdd(&hist_a[cls], 1ull);
                         atomicAdd(&hist_b[cls], 1ull);
-                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                        credit(g, out, G.new2old, c, C, cls);
                     }
-                    flush_hist(hist_b, C, out, __ldg(G.new2old + b), lane);
+                    flush_hist(g, hist_b, C, out, __ldg(G.new2old + b), lane);
                 }
                 // (A2) b in N(a) \ N(r), b > r
                 for (int64_t xb = a_up; xb < a_end; xb++) {
                     const uint32_t eb = __ldg(g.col + xb);
                     const uint32_t b = eb >> 2, fab = eb & 3u;
+                    if (!in_bounds(g, b < G.n)) break;
                     if (search_row(g.col, pb, pe, b)) continue;  // warp-uniform
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
+                    if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
                     // (1,2,2): c in N(a) after b, c not in N(r)
                     for (int64_t x = xb + 1 + lane; x < a_end; x += 32) {
                         const uint32_t ec = __ldg(g.col + x);
                         const uint32_t c = ec >> 2;
                         if (search_row(g.col, pb, pe, c)) continue;
                         const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, ec & 3u, pair_flags(g, b, c))];
-                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        if (!in_bounds(g, cls < (uint32_t)C)) continue;
                         atomicAdd(&hist_r[cls], 1ull);
                         atomicAdd(&hist_a[cls], 1ull);
                         atomicAdd(&hist_b[cls], 1ull);
-                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                        credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,2,3): c in N(b), c > r, not in N(r), not adjacent to a
                     const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
@@ -315,18 +350,18 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (search_row(g.col, pb, pe, c)) continue;
                         if (pair_flags(g, a, c)) continue;
                         const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, 0u, ec & 3u)];
-                        if (cls >= (uint32_t)C) { atomicExch(status, (int)VDMC_ERR_DEVICE_LIMIT); continue; }
+                        if (!in_bounds(g, cls < (uint32_t)C)) continue;
                         atomicAdd(&hist_r[cls], 1ull);
                         atomicAdd(&hist_a[cls], 1ull);
                         atomicAdd(&hist_b[cls], 1ull);
-                        atomicAdd((unsigned long long *)&out[(int64_t)__ldg(G.new2old + c) * C + cls], 1ull);
+                        credit(g, out, G.new2old, c, C, cls);
                     }
-                    flush_hist(hist_b, C, out, __ldg(G.new2old + b), lane);
+                    flush_hist(g, hist_b, C, out, __ldg(G.new2old + b), lane);
                 }
             }
-            flush_hist(hist_a, C, out, __ldg(G.new2old + a), lane);
+            flush_hist(g, hist_a, C, out, __ldg(G.new2old + a), lane);
         }
-        flush_hist(hist_r, C, out, __ldg(G.new2old + r), lane);
+        flush_hist(g, hist_r, C, out, __ldg(G.new2old + r), lane);
     }
 }
 
@@ -439,7 +474,7 @@ static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint
         if (st != VDMC_OK) return st;
     }
     if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
-    GraphDesc d{g->rowptr, g->col, g->pbeg, g->new2old, out, g->n, 0};
+    GraphDesc d{g->rowptr, g->col, g->pbeg, g->new2old, out, g->n, 0, g->nnz};
     return launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
 }
 
@@ -470,7 +505,7 @@ extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *byt
     VDMC_CUDA_TRY(cudaMalloc((void **)&d, sizeof(unsigned long long)));
     cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
     if (e == cudaSuccess && g->n > 0) {
-        Csr c{g->rowptr, g->col, g->pbeg};
+        Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
         work_bytes_kernel<<<1184, 256>>>(c, g->n, k, d);
         e = cudaGetLastError();
     }

@@ -29,6 +29,7 @@ struct GraphDesc {
     uint64_t *out;           // [n * C_k], original-id rows
     int32_t n;
     int32_t pad;
+    int64_t nnz;             // entries of col
 };
 
 struct vdmc_graph {
