@@ -61,18 +61,25 @@ typedef struct {
     int64_t arcs_kept;         /* distinct directed arcs */
     int64_t edges_u;           /* edges of G_U (a reciprocal pair is one edge) */
     int64_t reciprocal_pairs;  /* edges of G_U carrying arcs both ways */
-    int64_t num_tasks;         /* (root, depth-1 slice) work items */
+    int64_t num_tasks;         /* (root, depth-1 slice) work items of the warp kernel */
+    int64_t num_hub_roots;     /* roots handled by the root-per-CTA kernel */
     int64_t device_bytes;      /* bytes held on the device by this graph */
 } vdmc_graph_info_t;
 
-/* Launch schedule of the enumeration kernel.  Results never depend on it. */
+/* Launch schedule of the counting kernels.  Results never depend on it. */
 typedef struct {
-    int32_t a_chunk;          /* depth-1 neighbours of one root per task (>= 1);
-                                 a root with L such neighbours is split into
-                                 ceil(L / a_chunk) interleaved tasks */
-    int32_t warps_per_block;  /* 1..32 */
-    int32_t blocks_per_sm;    /* 0 = as many as fit */
-    int32_t reserved;
+    int32_t a_chunk;            /* warp-per-task kernel: depth-1 neighbours of one
+                                   root per task (>= 1); a root with L such
+                                   neighbours is split into ceil(L / a_chunk)
+                                   interleaved tasks */
+    int32_t warps_per_block;    /* warp-per-task kernel: 1..8 */
+    int32_t blocks_per_sm;      /* warp-per-task kernel: 0 = as many as fit */
+    int32_t hub_min_l;          /* roots with at least this many higher-rank
+                                   neighbours go to the root-per-CTA kernel;
+                                   0 = every root to the warp-per-task kernel */
+    int32_t hub_blocks_per_sm;  /* root-per-CTA kernel: CTAs per SM (>= 1); each
+                                   owns a scratch slot of about 4n + 52 tcap bytes */
+    int32_t reserved[3];
 } vdmc_schedule_t;
 
 /*

@@ -37,10 +37,11 @@
 #include <vector>
 
 #include "vdmc_internal.cuh"
+#include "device_common.cuh"
 
 namespace {
 
-vdmc_schedule_t g_sched = {16, 8, 0, 0};
+vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, {0, 0, 0}};
 std::mutex g_sched_mu;
 
 struct DevLut {
@@ -73,136 +74,25 @@ cudaError_t device_lut(int k, const uint8_t **out) {
 
 // ------------------------------------------------------------ tasks -----
 
+// roots with L >= hub_min_l (> 0) belong to the root-per-CTA kernel
 __global__ void task_counts(const int64_t *rowptr, const int64_t *pbeg, int32_t n, int32_t a_chunk,
-                            int64_t *cnt) {
+                            int32_t hub_min_l, int64_t *cnt) {
     int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int64_t L = rowptr[r + 1] - pbeg[r];
-    cnt[r] = L > 0 ? (L + a_chunk - 1) / a_chunk : 0;
+    const bool hub = hub_min_l > 0 && L >= hub_min_l;
+    cnt[r] = (L > 0 && !hub) ? (L + a_chunk - 1) / a_chunk : 0;
 }
 
 __global__ void task_fill(const int64_t *rowptr, const int64_t *pbeg, const int64_t *off, int32_t n,
-                          int32_t a_chunk, Task *tasks) {
+                          int32_t a_chunk, int32_t hub_min_l, Task *tasks) {
     int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int64_t L = rowptr[r + 1] - pbeg[r];
-    if (L <= 0) return;
+    if (L <= 0 || (hub_min_l > 0 && L >= hub_min_l)) return;
     int32_t t = (int32_t)((L + a_chunk - 1) / a_chunk);
     int64_t o = off[r];
     for (int32_t j = 0; j < t; j++) tasks[o + j] = Task{r, j, t, 0};
-}
-
-// ------------------------------------------------------- enumeration -----
-
-struct Csr {
-    const int64_t *__restrict__ rowptr;
-    const uint32_t *__restrict__ col;
-    const int64_t *__restrict__ pbeg;
-    int64_t n;
-    int64_t nnz;
-    int *status;  // device status word; also receives bounds violations
-};
-
-// Every data-dependent index is checked before use.  A violation (which a
-// correct CSR never produces) sets the status word and the access is
-// skipped, so a corrupted input cannot make the kernel fault.
-__device__ __forceinline__ bool in_bounds(const Csr &g, bool ok) {
-    if (!ok) atomicExch(g.status, (int)VDMC_ERR_DEVICE_LIMIT);
-    return ok;
-}
-
-// flags of neighbour v in the sorted entries col[lo, hi); 0 if absent.
-// A stored edge always has non-zero flags.
-__device__ __forceinline__ uint32_t search_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
-                                               uint32_t v) {
-    const uint32_t *p = col + lo;
-    int32_t len = (int32_t)(hi - lo);
-    while (len > 0) {
-        int32_t half = len >> 1;
-        uint32_t e = __ldg(p + half);
-        if ((e >> 2) < v) {
-            p += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    if (p < col + hi) {
-        uint32_t e = __ldg(p);
-        if ((e >> 2) == v) return e & 3u;
-    }
-    return 0u;
-}
-
-// first position in col[lo, hi) with neighbour rank > v
-__device__ __forceinline__ int64_t upper_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
-                                             uint32_t v) {
-    int32_t len = (int32_t)(hi - lo);
-    int64_t base = lo;
-    while (len > 0) {
-        int32_t half = len >> 1;
-        if ((__ldg(col + base + half) >> 2) <= v) {
-            base += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return base;
-}
-
-// flags of the pair (u, v): bit0 = arc u->v, bit1 = arc v->u; 0 = no edge.
-__device__ __forceinline__ uint32_t pair_flags(const Csr &g, uint32_t u, uint32_t v) {
-    if (!in_bounds(g, u < g.n && v < g.n)) return 0u;
-    int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
-    int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
-    if (!in_bounds(g, ub >= 0 && ub <= ue && ue <= g.nnz && vb >= 0 && vb <= ve && ve <= g.nnz)) return 0u;
-    if (ue - ub <= ve - vb) return search_row(g.col, ub, ue, v);
-    uint32_t f = search_row(g.col, vb, ve, u);
-    return ((f & 1u) << 1) | (f >> 1);
-}
-
-// Motif index of the ordered tuple (r, a, b) from the three pair flags.
-// Bit order (Fig. 1): (0,1) (0,2) (1,0) (1,2) (2,0) (2,1), MSB first.
-__device__ __forceinline__ uint32_t mask3(uint32_t fra, uint32_t frb, uint32_t fab) {
-    return ((fra & 1u) << 5) | ((frb & 1u) << 4) | ((fra >> 1) << 3) | ((fab & 1u) << 2) | ((frb >> 1) << 1) |
-           (fab >> 1);
-}
-
-// Motif index of (r, a, b, c): (0,1) (0,2) (0,3) (1,0) (1,2) (1,3) (2,0)
-// (2,1) (2,3) (3,0) (3,1) (3,2), MSB first.
-__device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t frc, uint32_t fab, uint32_t fac,
-                                          uint32_t fbc) {
-    return ((fra & 1u) << 11) | ((frb & 1u) << 10) | ((frc & 1u) << 9) | ((fra >> 1) << 8) | ((fab & 1u) << 7) |
-           ((fac & 1u) << 6) | ((frb >> 1) << 5) | ((fab >> 1) << 4) | ((fbc & 1u) << 3) | ((frc >> 1) << 2) |
-           ((fac >> 1) << 1) | (fbc >> 1);
-}
-
-// +1 for vertex (rank) v in column cls of its original-id row
-__device__ __forceinline__ void credit(const Csr &g, uint64_t *out, const int32_t *new2old, uint32_t v, int C,
-                                       uint32_t cls) {
-    if (!in_bounds(g, v < g.n)) return;
-    const int32_t o = __ldg(new2old + v);
-    if (!in_bounds(g, o >= 0 && o < g.n)) return;
-    atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], 1ull);
-}
-
-__device__ __forceinline__ void flush_hist(const Csr &g, unsigned long long *hist, int C, uint64_t *out,
-                                           int32_t orig, int lane) {
-    __syncwarp();
-    if (!in_bounds(g, orig >= 0 && orig < g.n)) {
-        for (int c = lane; c < C; c += 32) hist[c] = 0ull;
-        __syncwarp();
-        return;
-    }
-    for (int c = lane; c < C; c += 32) {
-        unsigned long long v = hist[c];
-        if (v) {
-            atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
-            hist[c] = 0ull;
-        }
-    }
-    __syncwarp();
 }
 
 template <int K>
@@ -435,8 +325,8 @@ void vdmc_current_schedule(vdmc_schedule_t *s) {
     *s = g_sched;
 }
 
-vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s) {
-    if (a_chunk < 1) return VDMC_ERR_INVALID_ARG;
+vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, cudaStream_t s) {
+    if (a_chunk < 1 || hub_min_l < 0) return VDMC_ERR_INVALID_ARG;
     cudaFree(g->tasks);
     g->tasks = nullptr;
     g->ntasks = 0;
@@ -444,7 +334,7 @@ vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s) {
     int64_t *cnt = nullptr;
     VDMC_CUDA_TRY(cudaMallocAsync((void **)&cnt, sizeof(int64_t) * ((size_t)n + 1), s));
     if (n > 0) {
-        task_counts<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, n, a_chunk, cnt);
+        task_counts<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, n, a_chunk, hub_min_l, cnt);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = vdmc_exclusive_scan_i64(cnt, cnt, n, s);
@@ -453,14 +343,14 @@ vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->tasks, sizeof(Task) * (size_t)(total ? total : 1));
     if (e == cudaSuccess && n > 0) {
-        task_fill<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, cnt, n, a_chunk, g->tasks);
+        task_fill<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, cnt, n, a_chunk, hub_min_l, g->tasks);
         e = cudaGetLastError();
     }
     cudaFreeAsync(cnt, s);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
     g->ntasks = total;
     g->tasks_a_chunk = a_chunk;
-    return VDMC_OK;
+    return vdmc_build_hubs(g, hub_min_l, s);
 }
 
 static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s) {
@@ -469,13 +359,26 @@ static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint
     const int C = k == 3 ? 13 : 199;
     vdmc_schedule_t sch;
     vdmc_current_schedule(&sch);
-    if (g->tasks_a_chunk != sch.a_chunk) {
-        vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, s);
+    if (g->tasks_a_chunk != sch.a_chunk || g->hub_min_l != sch.hub_min_l) {
+        vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, sch.hub_min_l, s);
         if (st != VDMC_OK) return st;
     }
     if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
     GraphDesc d{g->rowptr, g->col, g->pbeg, g->new2old, out, g->n, 0, g->nnz};
-    return launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
+    if (g->nhubs > 0) {
+        // the root-per-CTA kernel runs on the graph's side stream, overlapped
+        // with the warp kernel; the caller's stream waits for both
+        const uint8_t *lut = nullptr;
+        VDMC_CUDA_TRY(device_lut(k, &lut));
+        VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
+        VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        vdmc_status st = vdmc_hub_launch(g, k, out, lut, lo, hi, sch.hub_blocks_per_sm, g->side);
+        if (st != VDMC_OK) return st;
+        VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
+    }
+    vdmc_status st = launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
+    if (g->nhubs > 0) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
+    return st;
 }
 
 extern "C" vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {
@@ -519,7 +422,8 @@ extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *byt
 }
 
 extern "C" vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s) {
-    if (!s || s->a_chunk < 1 || s->warps_per_block < 1 || s->warps_per_block > 8 || s->blocks_per_sm < 0)
+    if (!s || s->a_chunk < 1 || s->warps_per_block < 1 || s->warps_per_block > 8 || s->blocks_per_sm < 0 ||
+        s->hub_min_l < 0 || s->hub_blocks_per_sm < 1 || s->hub_blocks_per_sm > 8)
         return VDMC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched = *s;

@@ -1,0 +1,127 @@
+// Device helpers shared by the enumeration kernels: CSR view, checked
+// accessors, adjacency search, motif index and credit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vdmc_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------- enumeration -----
+
+struct Csr {
+    const int64_t *__restrict__ rowptr;
+    const uint32_t *__restrict__ col;
+    const int64_t *__restrict__ pbeg;
+    int64_t n;
+    int64_t nnz;
+    int *status;  // device status word; also receives bounds violations
+};
+
+// Every data-dependent index is checked before use.  A violation (which a
+// correct CSR never produces) sets the status word and the access is
+// skipped, so a corrupted input cannot make the kernel fault.
+__device__ __forceinline__ bool in_bounds(const Csr &g, bool ok) {
+    if (!ok) atomicExch(g.status, (int)VDMC_ERR_DEVICE_LIMIT);
+    return ok;
+}
+
+// flags of neighbour v in the sorted entries col[lo, hi); 0 if absent.
+// A stored edge always has non-zero flags.
+__device__ __forceinline__ uint32_t search_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
+                                               uint32_t v) {
+    const uint32_t *p = col + lo;
+    int32_t len = (int32_t)(hi - lo);
+    while (len > 0) {
+        int32_t half = len >> 1;
+        uint32_t e = __ldg(p + half);
+        if ((e >> 2) < v) {
+            p += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    if (p < col + hi) {
+        uint32_t e = __ldg(p);
+        if ((e >> 2) == v) return e & 3u;
+    }
+    return 0u;
+}
+
+// first position in col[lo, hi) with neighbour rank > v
+__device__ __forceinline__ int64_t upper_row(const uint32_t *__restrict__ col, int64_t lo, int64_t hi,
+                                             uint32_t v) {
+    int32_t len = (int32_t)(hi - lo);
+    int64_t base = lo;
+    while (len > 0) {
+        int32_t half = len >> 1;
+        if ((__ldg(col + base + half) >> 2) <= v) {
+            base += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return base;
+}
+
+// flags of the pair (u, v): bit0 = arc u->v, bit1 = arc v->u; 0 = no edge.
+__device__ __forceinline__ uint32_t pair_flags(const Csr &g, uint32_t u, uint32_t v) {
+    if (!in_bounds(g, u < g.n && v < g.n)) return 0u;
+    int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
+    int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
+    if (!in_bounds(g, ub >= 0 && ub <= ue && ue <= g.nnz && vb >= 0 && vb <= ve && ve <= g.nnz)) return 0u;
+    if (ue - ub <= ve - vb) return search_row(g.col, ub, ue, v);
+    uint32_t f = search_row(g.col, vb, ve, u);
+    return ((f & 1u) << 1) | (f >> 1);
+}
+
+// Motif index of the ordered tuple (r, a, b) from the three pair flags.
+// Bit order (Fig. 1): (0,1) (0,2) (1,0) (1,2) (2,0) (2,1), MSB first.
+__device__ __forceinline__ uint32_t mask3(uint32_t fra, uint32_t frb, uint32_t fab) {
+    return ((fra & 1u) << 5) | ((frb & 1u) << 4) | ((fra >> 1) << 3) | ((fab & 1u) << 2) | ((frb >> 1) << 1) |
+           (fab >> 1);
+}
+
+// Motif index of (r, a, b, c): (0,1) (0,2) (0,3) (1,0) (1,2) (1,3) (2,0)
+// (2,1) (2,3) (3,0) (3,1) (3,2), MSB first.
+__device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t frc, uint32_t fab, uint32_t fac,
+                                          uint32_t fbc) {
+    return ((fra & 1u) << 11) | ((frb & 1u) << 10) | ((frc & 1u) << 9) | ((fra >> 1) << 8) | ((fab & 1u) << 7) |
+           ((fac & 1u) << 6) | ((frb >> 1) << 5) | ((fab >> 1) << 4) | ((fbc & 1u) << 3) | ((frc >> 1) << 2) |
+           ((fac >> 1) << 1) | (fbc >> 1);
+}
+
+// +1 for vertex (rank) v in column cls of its original-id row
+__device__ __forceinline__ void credit(const Csr &g, uint64_t *out, const int32_t *new2old, uint32_t v, int C,
+                                       uint32_t cls) {
+    if (!in_bounds(g, v < g.n)) return;
+    const int32_t o = __ldg(new2old + v);
+    if (!in_bounds(g, o >= 0 && o < g.n)) return;
+    atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], 1ull);
+}
+
+__device__ __forceinline__ void flush_hist(const Csr &g, unsigned long long *hist, int C, uint64_t *out,
+                                           int32_t orig, int lane) {
+    __syncwarp();
+    if (!in_bounds(g, orig >= 0 && orig < g.n)) {
+        for (int c = lane; c < C; c += 32) hist[c] = 0ull;
+        __syncwarp();
+        return;
+    }
+    for (int c = lane; c < C; c += 32) {
+        unsigned long long v = hist[c];
+        if (v) {
+            atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
+            hist[c] = 0ull;
+        }
+    }
+    __syncwarp();
+}
+
+
+}  // namespace

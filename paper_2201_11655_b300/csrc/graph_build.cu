@@ -197,6 +197,10 @@ void free_graph_buffers(vdmc_graph *g) {
     cudaFree(g->tasks);
     cudaFree(g->qhead);
     cudaFree(g->status);
+    vdmc_hub_free(g);
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
 }
 
 vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int on_device,
@@ -207,6 +211,9 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     VDMC_CUDA_TRY(cudaGetDevice(&g->device));
     VDMC_CUDA_TRY(cudaMalloc((void **)&g->qhead, sizeof(unsigned long long)));
     VDMC_CUDA_TRY(cudaMalloc((void **)&g->status, sizeof(int)));
+    VDMC_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+    VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+    VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
     VDMC_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), s));
 
     Tmp tmp(s);
@@ -339,7 +346,7 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
 
     vdmc_schedule_t sch;
     vdmc_current_schedule(&sch);
-    vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, s);
+    vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, sch.hub_min_l, s);
     if (st != VDMC_OK) return st;
     VDMC_CUDA_TRY(cudaStreamSynchronize(s));
     return VDMC_OK;
@@ -388,6 +395,8 @@ extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *i
     if (!g || !info) return VDMC_ERR_INVALID_ARG;
     *info = g->info;
     info->num_tasks = g->ntasks;
+    info->num_hub_roots = g->nhubs;
+    info->device_bytes += (int64_t)g->hub_scratch_bytes;
     return VDMC_OK;
 }
 

@@ -1,0 +1,917 @@
+// Root-per-CTA counting of high-degree roots (exact, no per-set loop for
+// star-like sets).
+//
+// For a root r with many higher-rank neighbours P = N+(r) (L = |P|), almost
+// all proper k-BFS(r) of the paper's enumeration ("The Algorithm"; Lemma 2
+// structures) are stars: sets whose non-root members are pairwise
+// non-adjacent.  The class of such a set (the isomorph-merged index of
+// Fig. 1) depends only on the 2-bit arc flags between the root and each
+// member -- the member's "colour".  So instead of visiting the O(L^3) stars
+// one at a time, this kernel counts them by colour and flag signatures, and
+// enumerates one by one only the sets that carry an edge between non-root
+// members (rare: the sub-graph H induced on P is sparse).  Every set of the
+// plain enumeration is accounted for exactly once and credited to each of
+// its members in the same class; results are bit-identical to the plain
+// kernel (count.cu), which handles the low-degree roots.
+//
+// Notation (root r fixed):
+//   P     positions 0..L-1 of N+(r) in rank order; colour(x) = flags(r, x)
+//   H     undirected graph induced on P; NH(x) its neighbours, h(u,v) the
+//         2-bit flags of the pair (bit 0: u -> v, bit 1: v -> u)
+//   Q     vertices of rank > r not adjacent to r; NQ(x) = N(x) n Q;
+//         NP(c) = N(c) n P for c in Q
+// k = 4 shapes with their counting rule:
+//   S1 (1,1,1) {x,y,z} c P: sets with 0 or 1 H-edge are counted per member
+//      by inclusion-exclusion over its H-neighbourhood; sets with 2 or 3
+//      H-edges (wedges, triangles of H) are enumerated.
+//   S2 (1,1,2) {x,y} c P, c in Q: c adjacent to exactly one of them is
+//      counted per (x, c) by signature; c adjacent to both is enumerated.
+//   S3 (1,2,2) x in P, {b,c} c NQ(x): counted per x by flag signature;
+//      b ~ c (triangle) is enumerated.
+//   S4 (1,2,3) x in P, b in NQ(x), c in NQ(b) \ N(x): counted per (x, b)
+//      and per (b, c) by signature; triangles x-b-c correct the counts.
+// k = 3: star {a,b} c P counted per member by colour; path a in P, b in
+// NQ(a) counted per (a) and per b by signature.
+//
+// Work per root is O(sum of the degrees of P and of its Q-neighbours +
+// enumerated exceptions) instead of O(number of sets).  Each CTA owns a
+// slot of scratch: a rank-indexed position map (-1 = not yet seen), compact
+// per-Q-vertex counters, the adjacency lists of H.  Waits: none; the only
+// cross-thread protocol is claim-by-atomicCAS followed by a barrier.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "vdmc_internal.cuh"
+#include "device_common.cuh"
+
+namespace {
+
+constexpr int HUB_WARPS = 8;
+constexpr int HUB_THREADS = HUB_WARPS * 32;
+constexpr int32_t CLAIMED = -2;  // posmap: claimed, index being written
+
+struct HubArgs {
+    Csr g;
+    const int32_t *new2old;
+    uint64_t *out;
+    const uint8_t *lut_g;
+    const int32_t *hubs;
+    int32_t nhubs;
+    int32_t rank_lo, rank_hi;
+    unsigned long long *qhead;
+    // per-slot scratch
+    int32_t *posmap;   // n per slot, all -1 between roots
+    uint32_t *qcnt;    // tcap * 9 per slot: P-neighbours of a Q vertex by (colour, flag)
+    uint32_t *wq;      // tcap * 3 per slot: Q-neighbours of a Q vertex by flag
+    int32_t *touched;  // tcap per slot
+    int32_t *hptr;     // lmax + 1 per slot
+    uint32_t *hlist;   // hcap per slot: (position << 2) | h(x, y)
+    uint32_t *hcx;     // lmax * 3 per slot: |NH(x)| by colour
+    uint32_t *wx;      // lmax * 3 per slot: |NQ(x)| by flag
+    uint32_t *htx;     // lmax * 9 per slot: |NH(x)| by (colour, flag)
+    uint32_t *npbuf;   // HUB_WARPS * lmax per slot
+    int64_t tcap, hcap, lmax;
+};
+
+__device__ __forceinline__ uint32_t swapf(uint32_t f) { return ((f & 1u) << 1) | (f >> 1); }
+
+// canonical index of an H-edge (y,z): colours cy, cz (1..3), flag f = h(y,z)
+__device__ __forceinline__ int etype(uint32_t cy, uint32_t cz, uint32_t f) {
+    if (cy > cz || (cy == cz && f == 2u)) {
+        uint32_t t = cy;
+        cy = cz;
+        cz = t;
+        f = swapf(f);
+    }
+    return (int)((cy - 1) * 9 + (cz - 1) * 3 + (f - 1));
+}
+
+// flags h(x, pos) if pos is in the sorted H-list hl[lo, hi) of x, else 0
+__device__ __forceinline__ uint32_t hlist_find(const uint32_t *hl, int32_t lo, int32_t hi, uint32_t pos) {
+    int32_t a = lo, b = hi;
+    while (a < b) {
+        int32_t mid = (a + b) >> 1;
+        uint32_t e = __ldcg(hl + mid);
+        if ((e >> 2) < pos) a = mid + 1;
+        else b = mid;
+    }
+    if (a < hi) {
+        uint32_t e = __ldcg(hl + a);
+        if ((e >> 2) == pos) return e & 3u;
+    }
+    return 0u;
+}
+
+// Where credits go: the output rows (original ids) and the checked view.
+struct Sink {
+    Csr g;
+    const int32_t *new2old;
+    uint64_t *out;
+};
+
+__device__ __forceinline__ void gadd(const Sink &A, uint32_t v, uint32_t cls, unsigned long long cnt, int C) {
+    if (cnt == 0ull) return;
+    if (!in_bounds(A.g, v < A.g.n && cls < (uint32_t)C)) return;
+    const int32_t o = __ldg(A.new2old + v);
+    if (!in_bounds(A.g, o >= 0 && o < A.g.n)) return;
+    atomicAdd((unsigned long long *)&A.out[(int64_t)o * C + cls], cnt);
+}
+
+__device__ __forceinline__ void sadd(unsigned long long *h, uint32_t cls, unsigned long long cnt) {
+    if (cnt) atomicAdd(&h[cls], cnt);
+}
+
+// exclusive scan of hptr[0, L) in place (hptr[L] = total), whole CTA
+__device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *total_out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t chunk = (L + HUB_THREADS - 1) / HUB_THREADS;
+    const int32_t beg = min(L, tid * chunk), end = min(L, beg + chunk);
+    int32_t s = 0;
+    for (int32_t p = beg; p < end; p++) s += __ldcg(hptr + p);
+    int32_t inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < HUB_WARPS ? warp_sums[lane] : 0, wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < HUB_WARPS) warp_sums[lane] = wi - w;
+        if (lane == HUB_WARPS - 1) *total_out = wi;
+    }
+    __syncthreads();
+    int32_t run = warp_sums[warp] + inc - s;
+    for (int32_t p = beg; p < end; p++) {
+        int32_t d = __ldcg(hptr + p);
+        hptr[p] = run;
+        run += d;
+    }
+    __syncthreads();
+    if (tid == 0) hptr[L] = *total_out;
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int K>
+__global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
+    constexpr int C = (K == 3) ? 13 : 199;
+    constexpr int NIDX = 1 << (K * (K - 1));
+    __shared__ uint8_t lut[NIDX];
+    __shared__ unsigned long long rootP[C], rootD[C];
+    __shared__ unsigned long long whist[HUB_WARPS][C];
+    __shared__ uint32_t esub[HUB_WARPS][27], eins[HUB_WARPS][27];
+    __shared__ unsigned long long Etype[27];
+    __shared__ unsigned long long Wtot[9];
+    __shared__ uint32_t ncol[3];
+    __shared__ int32_t s_root, s_tcount, s_total, s_skip;
+    __shared__ int32_t warp_sums[32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t slot = blockIdx.x;
+    const HubArgs A = args;  // local copy; no references into the parameter block
+    const Csr g = A.g;
+    const Sink S{g, A.new2old, A.out};
+    int32_t *posmap = A.posmap + slot * g.n;
+    uint32_t *qcnt = A.qcnt + slot * A.tcap * 9;
+    uint32_t *wq = A.wq + slot * A.tcap * 3;
+    int32_t *touched = A.touched + slot * A.tcap;
+    int32_t *hptr = A.hptr + slot * (A.lmax + 1);
+    uint32_t *hlist = A.hlist + slot * A.hcap;
+    uint32_t *hcx = A.hcx + slot * A.lmax * 3;
+    uint32_t *wx = A.wx + slot * A.lmax * 3;
+    uint32_t *htx = A.htx + slot * A.lmax * 9;
+    uint32_t *npbuf = A.npbuf + (slot * HUB_WARPS + warp) * A.lmax;
+    unsigned long long *hv = whist[warp];
+
+    for (int i = tid; i < NIDX; i += HUB_THREADS) lut[i] = A.lut_g[i];
+    for (int i = tid; i < HUB_WARPS * C; i += HUB_THREADS) (&whist[0][0])[i] = 0ull;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long q = atomicAdd(A.qhead, 1ull);
+            s_root = q < (unsigned long long)A.nhubs ? A.hubs[q] : -1;
+            s_tcount = 0;
+            s_skip = 0;
+        }
+        for (int i = tid; i < C; i += HUB_THREADS) {
+            rootP[i] = 0ull;
+            rootD[i] = 0ull;
+        }
+        if (tid < 27) Etype[tid] = 0ull;
+        if (tid < 9) Wtot[tid] = 0ull;
+        if (tid < 3) ncol[tid] = 0u;
+        __syncthreads();
+        const int32_t r = s_root;
+        if (r < 0) break;
+        if (r < A.rank_lo || r >= A.rank_hi || r >= g.n) continue;
+        const int64_t pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        if (!in_bounds(g, pb >= 0 && pb <= pe && pe <= g.nnz && pe - pb <= A.lmax)) continue;
+        const int32_t L = (int32_t)(pe - pb);
+        const uint32_t *P = g.col + pb;  // entries (rank << 2) | colour
+
+        // ---- phase 1: position map of P, colour counts
+        for (int32_t p = tid; p < L; p += HUB_THREADS) {
+            const uint32_t e = __ldg(P + p);
+            posmap[e >> 2] = p;
+            atomicAdd(&ncol[(e & 3u) - 1u], 1u);
+        }
+        __syncthreads();
+
+        // ---- phase 2: per x in P: |NH(x)|, colours of NH(x), |NQ(x)| by flag;
+        // claim the Q vertices (compact index per Q vertex)
+        for (int32_t i = warp; i < L; i += HUB_WARPS) {
+            const uint32_t x = __ldg(P + i) >> 2;
+            const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
+            const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
+            uint32_t dh = 0, hc0 = 0, hc1 = 0, hc2 = 0, w0 = 0, w1 = 0, w2 = 0;
+            for (int64_t e = xu + lane; e < xe; e += 32) {
+                const uint32_t ent = __ldg(g.col + e);
+                const uint32_t u = ent >> 2, f = ent & 3u;
+                const int32_t p = __ldcg(posmap + u);
+                if (p >= 0) {
+                    dh++;
+                    const uint32_t cu = __ldg(P + p) & 3u;
+                    hc0 += cu == 1u;
+                    hc1 += cu == 2u;
+                    hc2 += cu == 3u;
+                } else {
+                    w0 += f == 1u;
+                    w1 += f == 2u;
+                    w2 += f == 3u;
+                    if (p == -1 && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
+                        const int32_t t = atomicAdd(&s_tcount, 1);
+                        if (in_bounds(g, t < A.tcap)) {
+                            touched[t] = (int32_t)u;
+                            posmap[u] = -3 - t;
+                        }
+                    }
+                }
+            }
+            dh = warp_sum(dh);
+            hc0 = warp_sum(hc0); hc1 = warp_sum(hc1); hc2 = warp_sum(hc2);
+            w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+            if (lane == 0) {
+                hptr[i] = (int32_t)dh;
+                hcx[i * 3 + 0] = hc0; hcx[i * 3 + 1] = hc1; hcx[i * 3 + 2] = hc2;
+                wx[i * 3 + 0] = w0; wx[i * 3 + 1] = w1; wx[i * 3 + 2] = w2;
+            }
+        }
+        __syncthreads();
+        const int32_t tcount = s_tcount;
+        if (tcount > A.tcap) {
+            if (tid == 0) s_skip = 1;
+        }
+        cta_scan(hptr, L, warp_sums, &s_total);
+        if (!in_bounds(g, s_total <= A.hcap && s_skip == 0)) {
+            // leave the slot clean before giving up on this root
+            for (int32_t p = tid; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
+            for (int32_t t = tid; t < min(tcount, (int32_t)A.tcap); t += HUB_THREADS) posmap[touched[t]] = -1;
+            continue;
+        }
+
+        // ---- phase 3: H adjacency lists, H-edge types, per-Q-vertex P counts
+        for (int32_t i = warp; i < L; i += HUB_WARPS) {
+            const uint32_t ex = __ldg(P + i);
+            const uint32_t x = ex >> 2, fx = ex & 3u;
+            const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
+            const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
+            int32_t base = __ldcg(hptr + i);
+            uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+            for (int64_t e0 = xu; e0 < xe; e0 += 32) {
+                const int64_t e = e0 + lane;
+                const bool valid = e < xe;
+                const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+                const uint32_t u = ent >> 2, f = ent & 3u;
+                const int32_t p = valid ? __ldcg(posmap + u) : -1;
+                const bool isH = valid && p >= 0;
+                const uint32_t bal = __ballot_sync(0xffffffffu, isH);
+                if (isH) {
+                    hlist[base + __popc(bal & lt)] = ((uint32_t)p << 2) | f;
+                    const uint32_t cu = __ldg(P + p) & 3u;
+                    const uint32_t k9 = (cu - 1) * 3 + (f - 1);
+                    t0 += k9 == 0; t1 += k9 == 1; t2 += k9 == 2; t3 += k9 == 3; t4 += k9 == 4;
+                    t5 += k9 == 5; t6 += k9 == 6; t7 += k9 == 7; t8 += k9 == 8;
+                    if (i < p) atomicAdd(&Etype[etype(fx, cu, f)], 1ull);
+                } else if (valid && p <= -3) {
+                    const int64_t t = -3 - (int64_t)p;
+                    atomicAdd(qcnt + t * 9 + (fx - 1) * 3 + (f - 1), 1u);
+                }
+                base += __popc(bal);
+            }
+            t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2); t3 = warp_sum(t3); t4 = warp_sum(t4);
+            t5 = warp_sum(t5); t6 = warp_sum(t6); t7 = warp_sum(t7); t8 = warp_sum(t8);
+            if (lane == 0) {
+                uint32_t *h9 = htx + (int64_t)i * 9;
+                h9[0] = t0; h9[1] = t1; h9[2] = t2; h9[3] = t3; h9[4] = t4;
+                h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
+                for (int f = 0; f < 3; f++) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)__ldcg(wx + i * 3 + f));
+            }
+        }
+        __syncthreads();
+
+        // ---- phase 4 (k = 4): per Q vertex b, |NQ(b)| by flag
+        if (K == 4) {
+            for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
+                const uint32_t b = (uint32_t)__ldcg(touched + t);
+                const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
+                const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
+                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                for (int64_t e = bu + lane; e < be; e += 32) {
+                    const uint32_t ent = __ldg(g.col + e);
+                    if (__ldcg(posmap + (ent >> 2)) < 0) {
+                        const uint32_t f = ent & 3u;
+                        c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
+                    }
+                }
+                c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
+                if (lane == 0) {
+                    wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 5: per member v of P
+        for (int32_t i = warp; i < L; i += HUB_WARPS) {
+            const uint32_t ev = __ldg(P + i);
+            const uint32_t v = ev >> 2, al = ev & 3u;
+            const int32_t h0 = __ldcg(hptr + i), h1 = __ldcg(hptr + i + 1);
+            const int32_t dH = h1 - h0;
+            uint32_t hcv[3], Wv[3];
+            for (int k = 0; k < 3; k++) {
+                hcv[k] = __ldcg(hcx + i * 3 + k);
+                Wv[k] = __ldcg(wx + i * 3 + k);
+            }
+            const int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
+            const int64_t vu = upper_row(g.col, vb, ve, (uint32_t)r);
+
+            if (K == 3) {
+                // star, partner not adjacent: by colour
+                if (lane < 3) {
+                    const uint32_t be = lane + 1;
+                    const long long cnt = (long long)ncol[lane] - (al == be) - hcv[lane];
+                    const uint32_t cls = lut[mask3(al, be, 0u)];
+                    sadd(hv, cls, (unsigned long long)cnt);
+                    sadd(rootP, cls, (unsigned long long)cnt);
+                    // path with v as the depth-1 vertex: by flag
+                    const uint32_t cls2 = lut[mask3(al, 0u, be)];
+                    sadd(hv, cls2, Wv[lane]);
+                    sadd(rootD, cls2, Wv[lane]);
+                }
+                for (int32_t j = lane; j < dH; j += 32) {
+                    const uint32_t eu = __ldcg(hlist + h0 + j);
+                    const uint32_t cu = __ldg(P + (eu >> 2)) & 3u;
+                    const uint32_t cls = lut[mask3(al, cu, eu & 3u)];
+                    sadd(hv, cls, 1ull);
+                    sadd(rootP, cls, 1ull);
+                }
+            } else {
+                // -- S1 per-member counts: H-edges inside R_v = P \ N_H[v] by type
+                for (int k = lane; k < 27; k += 32) {
+                    esub[warp][k] = 0u;
+                    eins[warp][k] = 0u;
+                }
+                __syncwarp();
+                for (int32_t j = lane - 1; j < dH; j += 32) {
+                    const uint32_t up = j < 0 ? (uint32_t)i : (__ldcg(hlist + h0 + j) >> 2);
+                    const uint32_t cu = __ldg(P + up) & 3u;
+                    const int32_t u0 = __ldcg(hptr + up), u1 = __ldcg(hptr + up + 1);
+                    for (int32_t k = u0; k < u1; k++) {
+                        const uint32_t ew = __ldcg(hlist + k);
+                        const uint32_t w = ew >> 2;
+                        const int t = etype(cu, __ldg(P + w) & 3u, ew & 3u);
+                        atomicAdd(&esub[warp][t], 1u);
+                        if (up < w) {
+                            const bool inside = (up == (uint32_t)i) || (w == (uint32_t)i) ||
+                                                hlist_find(hlist, h0, h1, w) != 0u;
+                            if (inside) atomicAdd(&eins[warp][t], 1u);
+                        }
+                    }
+                }
+                __syncwarp();
+                // e_tau(R_v) = E_tau - (edges touching N_H[v])
+                for (int k = lane; k < 27; k += 32) {
+                    const long long e = (long long)Etype[k] - esub[warp][k] + eins[warp][k];
+                    esub[warp][k] = (uint32_t)e;
+                    const uint32_t be = k / 9 + 1, ga = (k / 3) % 3 + 1, f = k % 3 + 1;
+                    if (e > 0) {
+                        // S1 one H-edge (y,z) of type k, v isolated from both
+                        const uint32_t cls = lut[mask4(be, ga, al, f, 0u, 0u)];
+                        sadd(hv, cls, (unsigned long long)e);
+                        sadd(rootP, cls, (unsigned long long)e);
+                    }
+                }
+                __syncwarp();
+                if (lane < 6) {
+                    // S1 no H-edge: pairs {y,z} c R_v by colour pair minus H-edges
+                    const uint32_t be = lane < 3 ? 1u : (lane < 5 ? 2u : 3u);
+                    const uint32_t ga = lane < 3 ? (uint32_t)lane + 1 : (lane < 5 ? (uint32_t)lane - 1 : 3u);
+                    const long long ab = (long long)ncol[be - 1] - (al == be) - hcv[be - 1];
+                    const long long ag = (long long)ncol[ga - 1] - (al == ga) - hcv[ga - 1];
+                    long long pairs = be < ga ? ab * ag : ab * (ab - 1) / 2;
+                    for (uint32_t f = 1; f <= 3; f++) pairs -= (long long)esub[warp][(be - 1) * 9 + (ga - 1) * 3 + (f - 1)];
+                    const uint32_t cls = lut[mask4(al, be, ga, 0u, 0u, 0u)];
+                    sadd(hv, cls, (unsigned long long)pairs);
+                    sadd(rootP, cls, (unsigned long long)pairs);
+                }
+                // -- per H-neighbour u of v
+                for (int32_t j = lane; j < dH; j += 32) {
+                    const uint32_t eu = __ldcg(hlist + h0 + j);
+                    const uint32_t up = eu >> 2, fvu = eu & 3u;
+                    const uint32_t u = __ldg(P + up) >> 2, cu = __ldg(P + up) & 3u;
+                    const int32_t u0 = __ldcg(hptr + up), u1 = __ldcg(hptr + up + 1);
+                    uint32_t com[3] = {0u, 0u, 0u};
+                    for (int32_t k = u0; k < u1; k++) {
+                        const uint32_t w = __ldcg(hlist + k) >> 2;
+                        if (w != (uint32_t)i && hlist_find(hlist, h0, h1, w)) com[(__ldg(P + w) & 3u) - 1]++;
+                    }
+                    // S1 one H-edge (v,u), third member isolated, by its colour
+                    for (uint32_t ga = 1; ga <= 3; ga++) {
+                        const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - __ldcg(hcx + up * 3 + ga - 1) +
+                                              com[ga - 1];
+                        const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
+                        sadd(hv, cls, (unsigned long long)cnt);
+                        sadd(rootP, cls, (unsigned long long)cnt);
+                    }
+                    // S2 credit of u as the P member not adjacent to c, with
+                    // c in NQ(v) \ N(u): |NQ(v)| - |NQ(v) n N(u)| by h(v,c)
+                    uint32_t cq[3] = {0u, 0u, 0u};
+                    const int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
+                    if (ue - ub <= ve - vb) {
+                        for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r); e < ue; e++) {
+                            const uint32_t c = __ldg(g.col + e) >> 2;
+                            if (__ldcg(posmap + c) >= 0) continue;
+                            const uint32_t fvc = search_row(g.col, vu, ve, c);
+                            if (fvc) cq[fvc - 1]++;
+                        }
+                    } else {
+                        for (int64_t e = vu; e < ve; e++) {
+                            const uint32_t ec = __ldg(g.col + e);
+                            const uint32_t c = ec >> 2;
+                            if (__ldcg(posmap + c) >= 0) continue;
+                            if (search_row(g.col, ub, ue, c)) cq[(ec & 3u) - 1]++;
+                        }
+                    }
+                    for (uint32_t f = 1; f <= 3; f++) {
+                        const uint32_t cls = lut[mask4(al, cu, 0u, fvu, f, 0u)];
+                        gadd(S, u, cls, (unsigned long long)(Wv[f - 1] - cq[f - 1]), C);
+                    }
+                }
+                // -- S1 sets with two or three H-edges, v the centre
+                for (int32_t j1 = 0; j1 < dH; j1++) {
+                    const uint32_t e1 = __ldcg(hlist + h0 + j1);
+                    const uint32_t yp = e1 >> 2, fvy = e1 & 3u;
+                    const uint32_t cy = __ldg(P + yp) & 3u;
+                    const int32_t y0 = __ldcg(hptr + yp), y1 = __ldcg(hptr + yp + 1);
+                    for (int32_t j2 = j1 + 1 + lane; j2 < dH; j2 += 32) {
+                        const uint32_t e2 = __ldcg(hlist + h0 + j2);
+                        const uint32_t zp = e2 >> 2, fvz = e2 & 3u;
+                        const uint32_t cz = __ldg(P + zp) & 3u;
+                        const uint32_t fyz = hlist_find(hlist, y0, y1, zp);
+                        if (fyz == 0u || (uint32_t)i < yp) {
+                            const uint32_t cls = lut[mask4(al, cy, cz, fvy, fvz, fyz)];
+                            sadd(hv, cls, 1ull);
+                            gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
+                            gadd(S, __ldg(P + zp) >> 2, cls, 1ull, C);
+                            sadd(rootP, cls, 3ull);
+                        }
+                    }
+                }
+
+                // -- Q side: lanes over c in NQ(v)
+                long long Z[9];
+                for (int k = 0; k < 9; k++) Z[k] = 0;
+                unsigned long long Tp[9];  // S3 triangle pairs by (h(v,b), h(v,c)), b < c
+                for (int k = 0; k < 9; k++) Tp[k] = 0;
+                for (int64_t e = vu + lane; e < ve; e += 32) {
+                    const uint32_t ec = __ldg(g.col + e);
+                    const uint32_t c = ec >> 2, f = ec & 3u;
+                    const int32_t pc = __ldcg(posmap + c);
+                    if (pc >= 0) continue;
+                    if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                    const int64_t tc = -3 - (int64_t)pc;
+                    uint32_t q[9], np[3] = {0u, 0u, 0u};
+                    for (int k = 0; k < 9; k++) {
+                        q[k] = __ldcg(qcnt + tc * 9 + k);
+                        np[k / 3] += q[k];
+                    }
+                    // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
+                    uint32_t comT[9], comC[9];
+                    for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
+                    const int64_t cb = __ldg(g.rowptr + c), ce = __ldg(g.rowptr + c + 1);
+                    if (dH > 0) {
+                        if (ce - cb <= (int64_t)dH) {
+                            for (int64_t x = upper_row(g.col, cb, ce, (uint32_t)r); x < ce; x++) {
+                                const uint32_t ey = __ldg(g.col + x);
+                                const int32_t py = __ldcg(posmap + (ey >> 2));
+                                if (py < 0 || py == i) continue;
+                                const uint32_t fvy = hlist_find(hlist, h0, h1, (uint32_t)py);
+                                if (!fvy) continue;
+                                const uint32_t cy = __ldg(P + py) & 3u;
+                                comT[(cy - 1) * 3 + fvy - 1]++;
+                                comC[(cy - 1) * 3 + swapf(ey & 3u) - 1]++;
+                            }
+                        } else {
+                            for (int32_t j = 0; j < dH; j++) {
+                                const uint32_t eyv = __ldcg(hlist + h0 + j);
+                                const uint32_t yp = eyv >> 2;
+                                const uint32_t y = __ldg(P + yp) >> 2, cy = __ldg(P + yp) & 3u;
+                                const uint32_t fyc = pair_flags(g, y, c);
+                                if (!fyc) continue;
+                                comT[(cy - 1) * 3 + (eyv & 3u) - 1]++;
+                                comC[(cy - 1) * 3 + fyc - 1]++;
+                            }
+                        }
+                    }
+                    // S2 (x = v, c adjacent to v only): partner y by (colour, h(v,y))
+                    for (uint32_t be = 1; be <= 3; be++) {
+                        uint32_t combe = 0u;
+                        for (uint32_t fy = 1; fy <= 3; fy++) {
+                            const uint32_t k = (be - 1) * 3 + fy - 1;
+                            combe += comT[k];
+                            const long long cnt = (long long)__ldcg(htx + (int64_t)i * 9 + k) - comT[k];
+                            const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
+                            sadd(hv, cls, (unsigned long long)cnt);
+                            gadd(S, c, cls, (unsigned long long)cnt, C);
+                            sadd(rootD, cls, (unsigned long long)cnt);
+                        }
+                        const long long cnt = (long long)ncol[be - 1] - hcv[be - 1] - np[be - 1] + combe;
+                        const uint32_t cls = lut[mask4(al, be, 0u, 0u, f, 0u)];
+                        sadd(hv, cls, (unsigned long long)cnt);
+                        gadd(S, c, cls, (unsigned long long)cnt, C);
+                        sadd(rootD, cls, (unsigned long long)cnt);
+                    }
+                    // S2 credit of v as the P member not adjacent to c (collected in Z)
+                    for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k];
+                    Z[(al - 1) * 3 + f - 1] -= 1;
+                    // S3 / S4 with b = c: triangles v - c - c2, c2 in NQ(v)
+                    uint32_t T3[3] = {0u, 0u, 0u}, T4[3] = {0u, 0u, 0u};
+                    const bool scan_c = (ce - cb) <= (ve - vb);
+                    const int64_t s0 = scan_c ? upper_row(g.col, cb, ce, (uint32_t)r) : vu;
+                    const int64_t s1 = scan_c ? ce : ve;
+                    for (int64_t x = s0; x < s1; x++) {
+                        const uint32_t e2 = __ldg(g.col + x);
+                        const uint32_t c2 = e2 >> 2;
+                        if (c2 == c || __ldcg(posmap + c2) >= 0) continue;
+                        uint32_t fvc2, fcc2;
+                        if (scan_c) {
+                            fcc2 = e2 & 3u;
+                            fvc2 = search_row(g.col, vu, ve, c2);
+                        } else {
+                            fvc2 = e2 & 3u;
+                            fcc2 = search_row(g.col, cb, ce, c2);
+                        }
+                        if (!fvc2 || !fcc2) continue;
+                        T3[fvc2 - 1]++;
+                        T4[fcc2 - 1]++;
+                        const uint32_t cls3 = lut[mask4(al, 0u, 0u, f, fvc2, fcc2)];
+                        gadd(S, c, cls3, 1ull, C);
+                        if (c < c2) {
+                            sadd(hv, cls3, 1ull);
+                            sadd(rootD, cls3, 1ull);
+                            Tp[(f - 1) * 3 + fvc2 - 1]++;
+                        }
+                        const uint32_t cls4 = lut[mask4(al, 0u, 0u, f, 0u, fcc2)];
+                        gadd(S, c, cls4, ~0ull, C);   // -1: correction of the per-(c, c2) S4 count
+                        gadd(S, c2, cls4, ~0ull, C);
+                    }
+                    for (uint32_t f2 = 1; f2 <= 3; f2++) {
+                        // S3 credit of c: partners in NQ(v) not adjacent to c
+                        const long long cnt3 = (long long)Wv[f2 - 1] - (f == f2) - T3[f2 - 1];
+                        gadd(S, c, lut[mask4(al, 0u, 0u, f, f2, 0u)], (unsigned long long)cnt3, C);
+                        // S4 with (x, b) = (v, c): c's Q-neighbours not adjacent to v
+                        const long long cnt4 = (long long)__ldcg(wq + tc * 3 + f2 - 1) - T4[f2 - 1];
+                        const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
+                        sadd(hv, cls, (unsigned long long)cnt4);
+                        sadd(rootD, cls, (unsigned long long)cnt4);
+                    }
+                }
+                for (int k = 0; k < 9; k++) {
+                    Z[k] = warp_sum(Z[k]);
+                    Tp[k] = warp_sum(Tp[k]);
+                }
+                // S2 credit of v as the non-adjacent P member (x not in N_H[v])
+                if (lane < 9) {
+                    long long wsum = 0;
+                    for (int32_t j = -1; j < dH; j++) {
+                        const uint32_t xp = j < 0 ? (uint32_t)i : (__ldcg(hlist + h0 + j) >> 2);
+                        if ((__ldg(P + xp) & 3u) == (uint32_t)(lane / 3 + 1)) wsum += __ldcg(wx + xp * 3 + lane % 3);
+                    }
+                    const long long base = (long long)Wtot[lane] - wsum - Z[lane];
+                    const uint32_t cls = lut[mask4((uint32_t)(lane / 3 + 1), al, 0u, 0u, (uint32_t)(lane % 3 + 1), 0u)];
+                    sadd(hv, cls, (unsigned long long)base);
+                }
+                // S3 credit of v and r: pairs {b, c} c NQ(v) by flags, minus triangles
+                if (lane < 6) {
+                    const uint32_t f1 = lane < 3 ? 1u : (lane < 5 ? 2u : 3u);
+                    const uint32_t f2 = lane < 3 ? (uint32_t)lane + 1 : (lane < 5 ? (uint32_t)lane - 1 : 3u);
+                    long long pairs = f1 < f2 ? (long long)Wv[f1 - 1] * Wv[f2 - 1]
+                                              : (long long)Wv[f1 - 1] * ((long long)Wv[f1 - 1] - 1) / 2;
+                    pairs -= (long long)Tp[(f1 - 1) * 3 + f2 - 1];
+                    if (f1 != f2) pairs -= (long long)Tp[(f2 - 1) * 3 + f1 - 1];
+                    const uint32_t cls = lut[mask4(al, 0u, 0u, f1, f2, 0u)];
+                    sadd(hv, cls, (unsigned long long)pairs);
+                    sadd(rootD, cls, (unsigned long long)pairs);
+                }
+            }
+            __syncwarp();
+            flush_hist(g, hv, C, A.out, __ldg(A.new2old + v), lane);
+        }
+        __syncthreads();
+
+        // ---- phase 6: per Q vertex b
+        for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
+            const uint32_t b = (uint32_t)__ldcg(touched + t);
+            uint32_t q[9];
+            uint32_t npb = 0;
+            for (int k = 0; k < 9; k++) {
+                q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
+                npb += q[k];
+            }
+            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
+            const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
+            if (K == 3) {
+                // path with b at depth 2: by (colour, flag) of its P neighbours
+                if (lane < 9) {
+                    const uint32_t cls = lut[mask3((uint32_t)(lane / 3 + 1), 0u, (uint32_t)(lane % 3 + 1))];
+                    gadd(S, b, cls, q[lane], C);
+                }
+            } else {
+                // S4 credit of b: P neighbours x by (colour, h(x,b)), Q neighbours by flag
+                if (lane < 27) {
+                    const int k = lane / 3, g3 = lane % 3;
+                    const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
+                    gadd(S, b, cls, (unsigned long long)q[k] * __ldcg(wq + (int64_t)t * 3 + g3), C);
+                }
+                // S4 credit of each c in NQ(b)
+                for (int64_t e = bu + lane; e < be; e += 32) {
+                    const uint32_t ent = __ldg(g.col + e);
+                    const uint32_t c = ent >> 2;
+                    if (__ldcg(posmap + c) >= 0) continue;
+                    const uint32_t gg = ent & 3u;
+                    for (int k = 0; k < 9; k++)
+                        if (q[k]) gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], q[k], C);
+                }
+                // S2 with b adjacent to two members x, y of P: enumerate
+                if (npb >= 2 && in_bounds(g, npb <= (uint32_t)A.lmax)) {
+                    int32_t cnt = 0;
+                    for (int64_t e0 = bu; e0 < be; e0 += 32) {
+                        const int64_t e = e0 + lane;
+                        const bool valid = e < be;
+                        const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+                        const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
+                        const bool isP = valid && p >= 0;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, isP);
+                        if (isP && cnt + __popc(bal & lt) < A.lmax)
+                            npbuf[cnt + __popc(bal & lt)] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
+                        cnt += __popc(bal);
+                    }
+                    __syncwarp();
+                    cnt = min(cnt, (int32_t)A.lmax);
+                    for (int32_t j1 = 0; j1 < cnt; j1++) {
+                        const uint32_t e1 = __ldcg(npbuf + j1);
+                        const uint32_t xp = e1 >> 2, fxb = e1 & 3u;
+                        const uint32_t cx = __ldg(P + xp) & 3u;
+                        const int32_t x0 = __ldcg(hptr + xp), x1 = __ldcg(hptr + xp + 1);
+                        for (int32_t j2 = j1 + 1 + lane; j2 < cnt; j2 += 32) {
+                            const uint32_t e2 = __ldcg(npbuf + j2);
+                            const uint32_t yp = e2 >> 2, fyb = e2 & 3u;
+                            const uint32_t cy = __ldg(P + yp) & 3u;
+                            const uint32_t fxy = hlist_find(hlist, x0, x1, yp);
+                            const uint32_t cls = lut[mask4(cx, cy, 0u, fxy, fxb, fyb)];
+                            gadd(S, __ldg(P + xp) >> 2, cls, 1ull, C);
+                            gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
+                            gadd(S, b, cls, 1ull, C);
+                            sadd(rootD, cls, 1ull);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- phase 7: root credit, reset the slot
+        {
+            const int32_t orig = __ldg(A.new2old + r);
+            for (int c = tid; c < C; c += HUB_THREADS) {
+                const unsigned long long v = rootP[c] / (K == 3 ? 2ull : 3ull) + rootD[c];
+                if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
+            }
+        }
+        for (int32_t p = tid; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
+        for (int32_t t = tid; t < tcount; t += HUB_THREADS) {
+            posmap[__ldcg(touched + t)] = -1;
+            for (int k = 0; k < 9; k++) qcnt[(int64_t)t * 9 + k] = 0u;
+        }
+    }
+}
+
+__global__ void fill_i32(int32_t *p, int64_t n, int32_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host --
+
+namespace {
+
+__global__ void hub_flags(const int64_t *rowptr, const int64_t *pbeg, int32_t n, int32_t min_l, uint32_t *flag) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t L = rowptr[r + 1] - pbeg[r];
+    flag[r] = (min_l > 0 && L >= min_l) ? 1u : 0u;
+}
+
+__global__ void hub_compact(const uint32_t *flag, const uint32_t *pos, int32_t n, int32_t *hubs) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n && flag[r]) hubs[pos[r]] = r;
+}
+
+// per hub root: L, sum over P of min(d(x), L) (bound on its H lists) and of
+// d(x) (bound on its Q vertices)
+__global__ void hub_sizes(const int64_t *rowptr, const uint32_t *col, const int64_t *pbeg, const int32_t *hubs,
+                          int32_t nhubs, unsigned long long *mx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nhubs) return;
+    const int32_t r = hubs[w];
+    const int64_t pb = pbeg[r], pe = rowptr[r + 1];
+    const int64_t L = pe - pb;
+    unsigned long long s1 = 0, s2 = 0;
+    for (int64_t e = pb + lane; e < pe; e += 32) {
+        const uint32_t x = col[e] >> 2;
+        const int64_t d = rowptr[x + 1] - rowptr[x];
+        s1 += (unsigned long long)(d < L ? d : L);
+        s2 += (unsigned long long)d;
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+        atomicMax(&mx[0], (unsigned long long)L);
+        atomicMax(&mx[1], s1);
+        atomicMax(&mx[2], s2);
+    }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+void vdmc_hub_free(vdmc_graph *g) {
+    cudaFree(g->hubs);
+    cudaFree(g->hub_scratch);
+    cudaFree(g->hub_qhead);
+    g->hubs = nullptr;
+    g->hub_scratch = nullptr;
+    g->hub_qhead = nullptr;
+    g->nhubs = 0;
+    g->hub_slots = 0;
+    g->hub_scratch_bytes = 0;
+}
+
+vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
+    vdmc_hub_free(g);
+    g->hub_min_l = min_l;
+    const int32_t n = g->n;
+    if (min_l <= 0 || n == 0) return VDMC_OK;
+    uint32_t *flag = nullptr, *pos = nullptr;
+    VDMC_CUDA_TRY(cudaMallocAsync((void **)&flag, sizeof(uint32_t) * (size_t)n, s));
+    cudaError_t e = cudaMallocAsync((void **)&pos, sizeof(uint32_t) * ((size_t)n + 1), s);
+    unsigned long long *mx = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mx, sizeof(unsigned long long) * 3, s);
+    if (e == cudaSuccess) {
+        hub_flags<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, n, min_l, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = vdmc_exclusive_scan_u32(flag, pos, n, s);
+    uint32_t nh = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nh, pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && nh > 0) {
+        e = cudaMalloc((void **)&g->hubs, sizeof(int32_t) * nh);
+        if (e == cudaSuccess) {
+            hub_compact<<<(n + 255) / 256, 256, 0, s>>>(flag, pos, n, g->hubs);
+            e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 3, s);
+        }
+        if (e == cudaSuccess) {
+            hub_sizes<<<(unsigned)((nh * 32 + 255) / 256), 256, 0, s>>>(g->rowptr, g->col, g->pbeg, g->hubs, (int32_t)nh, mx);
+            e = cudaGetLastError();
+        }
+        unsigned long long h[3] = {0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, mx, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        g->hub_lmax = (int64_t)h[0];
+        g->hub_hcap = std::max<int64_t>(1, (int64_t)h[1]);
+        g->hub_tcap = std::max<int64_t>(1, std::min<int64_t>((int64_t)n, (int64_t)h[2]));
+        g->nhubs = (int32_t)nh;
+    }
+    cudaFreeAsync(flag, s);
+    cudaFreeAsync(pos, s);
+    cudaFreeAsync(mx, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
+    return VDMC_OK;
+}
+
+namespace {
+
+struct HubLayout {
+    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npbuf, total;
+};
+
+HubLayout hub_layout(const vdmc_graph *g, int slots) {
+    HubLayout L{};
+    size_t o = 0;
+    const size_t S = (size_t)slots, n = (size_t)g->n, t = (size_t)g->hub_tcap, lm = (size_t)g->hub_lmax;
+    L.posmap = o; o += align256(S * n * 4);
+    L.qcnt = o; o += align256(S * t * 9 * 4);
+    L.wq = o; o += align256(S * t * 3 * 4);
+    L.touched = o; o += align256(S * t * 4);
+    L.hptr = o; o += align256(S * (lm + 1) * 4);
+    L.hlist = o; o += align256(S * (size_t)g->hub_hcap * 4);
+    L.hcx = o; o += align256(S * lm * 3 * 4);
+    L.wx = o; o += align256(S * lm * 3 * 4);
+    L.htx = o; o += align256(S * lm * 9 * 4);
+    L.npbuf = o; o += align256(S * HUB_WARPS * lm * 4);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+int vdmc_hub_count(const vdmc_graph *g) { return g->nhubs; }
+
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *lut, int32_t lo, int32_t hi,
+                            int blocks_per_sm, cudaStream_t s) {
+    if (g->nhubs <= 0) return VDMC_OK;
+    int dev = 0, sms = 0;
+    VDMC_CUDA_TRY(cudaGetDevice(&dev));
+    VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int slots = std::max(1, sms * std::max(1, blocks_per_sm));
+    slots = std::min(slots, g->nhubs);
+    if (slots > g->hub_slots) {
+        // (re)allocate the per-slot scratch; posmap starts at -1, counters at 0
+        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(g->hub_scratch);
+        g->hub_scratch = nullptr;
+        g->hub_slots = 0;
+        HubLayout L = hub_layout(g, slots);
+        VDMC_CUDA_TRY(cudaMalloc(&g->hub_scratch, L.total));
+        if (!g->hub_qhead) VDMC_CUDA_TRY(cudaMalloc((void **)&g->hub_qhead, sizeof(unsigned long long)));
+        char *base = (char *)g->hub_scratch;
+        VDMC_CUDA_TRY(cudaMemsetAsync(base + L.qcnt, 0, L.wq - L.qcnt, s));
+        const int64_t np = (int64_t)slots * g->n;
+        if (np > 0) {
+            fill_i32<<<(unsigned)((np + 255) / 256), 256, 0, s>>>((int32_t *)(base + L.posmap), np, -1);
+            VDMC_CUDA_TRY(cudaGetLastError());
+        }
+        g->hub_slots = slots;
+        g->hub_scratch_bytes = L.total;
+    }
+    HubLayout L = hub_layout(g, g->hub_slots);
+    char *base = (char *)g->hub_scratch;
+    HubArgs A;
+    A.g = Csr{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
+    A.new2old = g->new2old;
+    A.out = out;
+    A.lut_g = lut;
+    A.hubs = g->hubs;
+    A.nhubs = g->nhubs;
+    A.rank_lo = lo;
+    A.rank_hi = hi;
+    A.qhead = g->hub_qhead;
+    A.posmap = (int32_t *)(base + L.posmap);
+    A.qcnt = (uint32_t *)(base + L.qcnt);
+    A.wq = (uint32_t *)(base + L.wq);
+    A.touched = (int32_t *)(base + L.touched);
+    A.hptr = (int32_t *)(base + L.hptr);
+    A.hlist = (uint32_t *)(base + L.hlist);
+    A.hcx = (uint32_t *)(base + L.hcx);
+    A.wx = (uint32_t *)(base + L.wx);
+    A.htx = (uint32_t *)(base + L.htx);
+    A.npbuf = (uint32_t *)(base + L.npbuf);
+    A.tcap = g->hub_tcap;
+    A.hcap = g->hub_hcap;
+    A.lmax = g->hub_lmax;
+    VDMC_CUDA_TRY(cudaMemsetAsync(g->hub_qhead, 0, sizeof(unsigned long long), s));
+    if (k == 3) hub_kernel<3><<<(unsigned)slots, HUB_THREADS, 0, s>>>(A);
+    else hub_kernel<4><<<(unsigned)slots, HUB_THREADS, 0, s>>>(A);
+    VDMC_CUDA_TRY(cudaGetLastError());
+    return VDMC_OK;
+}

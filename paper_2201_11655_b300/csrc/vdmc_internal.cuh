@@ -47,6 +47,17 @@ struct vdmc_graph {
     unsigned long long *qhead;   // work-queue cursor
     int *status;                 // device status word
     vdmc_graph_info_t info;
+    // root-per-CTA kernel (hub.cu)
+    int32_t *hubs;               // ranks of the roots it handles, heavy first
+    int32_t nhubs;
+    int32_t hub_min_l;
+    int64_t hub_lmax, hub_hcap, hub_tcap;
+    int hub_slots;
+    void *hub_scratch;
+    size_t hub_scratch_bytes;
+    unsigned long long *hub_qhead;
+    cudaStream_t side;           // second stream: the two kernels overlap
+    cudaEvent_t ev_fork, ev_join;
 };
 
 // ---- status helpers ----
@@ -78,5 +89,11 @@ const uint8_t *vdmc_host_lut(int k);
 const uint16_t *vdmc_host_canon(int k, int *num_classes);
 
 // ---- schedule / tasks (count.cu) ----
-vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, cudaStream_t s);
+vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, cudaStream_t s);
 void vdmc_current_schedule(vdmc_schedule_t *s);
+
+// ---- root-per-CTA kernel (hub.cu) ----
+vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *lut, int32_t lo, int32_t hi,
+                            int blocks_per_sm, cudaStream_t s);
+void vdmc_hub_free(vdmc_graph *g);

@@ -34,7 +34,7 @@ class GraphInfo(ctypes.Structure):
         ("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("arcs_in", ctypes.c_int64),
         ("self_loops", ctypes.c_int64), ("duplicate_arcs", ctypes.c_int64), ("arcs_kept", ctypes.c_int64),
         ("edges_u", ctypes.c_int64), ("reciprocal_pairs", ctypes.c_int64), ("num_tasks", ctypes.c_int64),
-        ("device_bytes", ctypes.c_int64),
+        ("num_hub_roots", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -43,7 +43,10 @@ class GraphInfo(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("a_chunk", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("hub_min_l", ctypes.c_int32),
+                ("hub_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+SCHEDULE_KEYS = ("a_chunk", "warps_per_block", "blocks_per_sm", "hub_min_l", "hub_blocks_per_sm")
 
 
 _LIB = None
@@ -238,15 +241,18 @@ def count_batch(graphs, k: int, outs=None, stream=None):
     return outs
 
 
-def set_schedule(a_chunk=None, warps_per_block=None, blocks_per_sm=None):
+def set_schedule(**kw):
+    """Set any of the launch-schedule knobs (see vdmc_schedule_t); the rest keep their values."""
+    bad = set(kw) - set(SCHEDULE_KEYS)
+    if bad:
+        raise TypeError("unknown schedule keys %s" % sorted(bad))
     cur = get_schedule()
-    s = Schedule(a_chunk if a_chunk is not None else cur["a_chunk"],
-                 warps_per_block if warps_per_block is not None else cur["warps_per_block"],
-                 blocks_per_sm if blocks_per_sm is not None else cur["blocks_per_sm"], 0)
+    cur.update({k: v for k, v in kw.items() if v is not None})
+    s = Schedule(*[int(cur[k]) for k in SCHEDULE_KEYS])
     _check(_lib().vdmc_set_schedule(ctypes.byref(s)), "vdmc_set_schedule")
 
 
 def get_schedule() -> dict:
     s = Schedule()
     _check(_lib().vdmc_get_schedule(ctypes.byref(s)), "vdmc_get_schedule")
-    return {"a_chunk": s.a_chunk, "warps_per_block": s.warps_per_block, "blocks_per_sm": s.blocks_per_sm}
+    return {k: getattr(s, k) for k in SCHEDULE_KEYS}

@@ -71,14 +71,17 @@ def test_invalid_args_rejected_on_host(lib):
     assert lib.vdmc_graph_create(5, 3, None, None, 0, None, ctypes.byref(h)) == 1
     assert lib.vdmc_count(None, 3, None, None) == 1
     assert lib.vdmc_graph_info(None, None) == 1
-    s = vdmc.Schedule(0, 8, 0, 0)
+    s = vdmc.Schedule(0, 8, 0, 0, 1)
+    assert lib.vdmc_set_schedule(ctypes.byref(s)) == 1
+    s = vdmc.Schedule(4, 8, 0, 0, 0)  # hub_blocks_per_sm must be >= 1
     assert lib.vdmc_set_schedule(ctypes.byref(s)) == 1
 
 
 def test_schedule_roundtrip(lib):
     old = vdmc.get_schedule()
     try:
-        vdmc.set_schedule(a_chunk=3, warps_per_block=4, blocks_per_sm=2)
-        assert vdmc.get_schedule() == {"a_chunk": 3, "warps_per_block": 4, "blocks_per_sm": 2}
+        vdmc.set_schedule(a_chunk=3, warps_per_block=4, blocks_per_sm=2, hub_min_l=7, hub_blocks_per_sm=2)
+        assert vdmc.get_schedule() == {"a_chunk": 3, "warps_per_block": 4, "blocks_per_sm": 2,
+                                       "hub_min_l": 7, "hub_blocks_per_sm": 2}
     finally:
         vdmc.set_schedule(**old)

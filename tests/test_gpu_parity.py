@@ -151,12 +151,51 @@ def test_schedules_do_not_change_results():
     want = {k: O.count(n, s, d, k)[0] for k in (3, 4)}
     old = vdmc.get_schedule()
     try:
-        for a_chunk, warps, bps in ((1, 8, 0), (7, 4, 1), (64, 1, 0), (1000, 2, 3)):
-            vdmc.set_schedule(a_chunk=a_chunk, warps_per_block=warps, blocks_per_sm=bps)
+        for a_chunk, warps, bps, hub, hbps in ((1, 8, 0, 0, 1), (7, 4, 1, 0, 1), (64, 1, 0, 3, 2),
+                                               (1000, 2, 3, 1, 1), (16, 8, 0, 20, 3)):
+            vdmc.set_schedule(a_chunk=a_chunk, warps_per_block=warps, blocks_per_sm=bps, hub_min_l=hub,
+                              hub_blocks_per_sm=hbps)
             for k in (3, 4):
                 np.testing.assert_array_equal(gpu_count(n, s, d, k), want[k])
     finally:
         vdmc.set_schedule(**old)
+
+
+@pytest.fixture
+def schedule():
+    from paper_2201_11655_b300 import vdmc
+    old = vdmc.get_schedule()
+    yield vdmc
+    vdmc.set_schedule(**old)
+
+
+@pytest.mark.parametrize("hub_min_l", [0, 1])
+@pytest.mark.parametrize("seed", range(10))
+def test_root_per_cta_kernel_vs_oracle(schedule, hub_min_l, seed):
+    # hub_min_l = 1 sends every root to the root-per-CTA (signature counting)
+    # kernel, 0 every root to the warp-per-task (plain enumeration) kernel.
+    schedule.set_schedule(hub_min_l=hub_min_l)
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(4, 250))
+    kind = seed % 3
+    if kind == 0:
+        n, s, d = synth.gnp(n, float(rng.uniform(0.02, 0.4)), seed)
+    elif kind == 1:
+        n, s, d = synth.chung_lu(n, float(rng.uniform(1.0, 8.0)), float(rng.uniform(2.05, 2.6)), seed,
+                                 reciprocity=float(rng.uniform(0, 0.6)))
+    else:
+        # dense core + sparse periphery: many H-edges, wedges and triangles
+        n1, s1, d1 = synth.gnp(min(n, 30), 0.5, seed)
+        n2, s2, d2 = synth.chung_lu(n, 3.0, 2.2, seed + 1, reciprocity=0.3)
+        s, d = np.concatenate([s1, s2]), np.concatenate([d1, d2])
+    check(n, s, d)
+
+
+def test_root_per_cta_kernel_medium_powerlaw(schedule):
+    n, s, d = synth.chung_lu(4000, 5.0, 2.1, 31, reciprocity=0.25)
+    for hub in (1, 16, 200):
+        schedule.set_schedule(hub_min_l=hub)
+        check(n, s, d)
 
 
 # ---------------------------------------------------------------- edges --
