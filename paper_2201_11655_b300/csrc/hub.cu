@@ -71,8 +71,9 @@ struct HubArgs {
     uint32_t *hcx;     // lmax * 3 per slot: |NH(x)| by colour
     uint32_t *wx;      // lmax * 3 per slot: |NQ(x)| by flag
     uint32_t *htx;     // lmax * 9 per slot: |NH(x)| by (colour, flag)
-    uint32_t *npbuf;   // HUB_WARPS * lmax per slot
-    int64_t tcap, hcap, lmax;
+    int32_t *npoff;    // tcap + 1 per slot: offsets of the NP lists
+    uint32_t *nplist;  // npcap per slot: (position << 2) | h(x, b)
+    int64_t tcap, hcap, lmax, npcap;
 };
 
 __device__ __forceinline__ uint32_t swapf(uint32_t f) { return ((f & 1u) << 1) | (f >> 1); }
@@ -158,6 +159,16 @@ __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *
     __syncthreads();
 }
 
+// return the slot to its resting state (posmap -1, counters 0)
+__device__ void reset_slot(int32_t *posmap, uint32_t *qcnt, const int32_t *touched, const uint32_t *P, int32_t L,
+                           int32_t tcount) {
+    for (int32_t p = threadIdx.x; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
+    for (int32_t t = threadIdx.x; t < tcount; t += HUB_THREADS) {
+        posmap[__ldcg(touched + t)] = -1;
+        for (int k = 0; k < 9; k++) qcnt[(int64_t)t * 9 + k] = 0u;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -193,7 +204,8 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
     uint32_t *hcx = A.hcx + slot * A.lmax * 3;
     uint32_t *wx = A.wx + slot * A.lmax * 3;
     uint32_t *htx = A.htx + slot * A.lmax * 9;
-    uint32_t *npbuf = A.npbuf + (slot * HUB_WARPS + warp) * A.lmax;
+    int32_t *npoff = A.npoff + slot * (A.tcap + 1);
+    uint32_t *nplist = A.nplist + slot * A.npcap;
     unsigned long long *hv = whist[warp];
 
     for (int i = tid; i < NIDX; i += HUB_THREADS) lut[i] = A.lut_g[i];
@@ -278,8 +290,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
         cta_scan(hptr, L, warp_sums, &s_total);
         if (!in_bounds(g, s_total <= A.hcap && s_skip == 0)) {
             // leave the slot clean before giving up on this root
-            for (int32_t p = tid; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
-            for (int32_t t = tid; t < min(tcount, (int32_t)A.tcap); t += HUB_THREADS) posmap[touched[t]] = -1;
+            reset_slot(posmap, qcnt, touched, P, L, min(tcount, (int32_t)A.tcap));
             continue;
         }
 
@@ -323,27 +334,50 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
         }
         __syncthreads();
 
-        // ---- phase 4 (k = 4): per Q vertex b, |NQ(b)| by flag
-        if (K == 4) {
-            for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
-                const uint32_t b = (uint32_t)__ldcg(touched + t);
-                const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
-                const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-                uint32_t c0 = 0, c1 = 0, c2 = 0;
-                for (int64_t e = bu + lane; e < be; e += 32) {
-                    const uint32_t ent = __ldg(g.col + e);
-                    if (__ldcg(posmap + (ent >> 2)) < 0) {
-                        const uint32_t f = ent & 3u;
-                        c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
-                    }
+        // ---- phase 4: NP(b) lists (P-neighbours of each Q vertex b, in
+        // position order, read from b's own row) and |NQ(b)| by flag
+        for (int32_t t = tid; t < tcount; t += HUB_THREADS) {
+            uint32_t s9 = 0;
+            for (int k = 0; k < 9; k++) s9 += __ldcg(qcnt + (int64_t)t * 9 + k);
+            npoff[t] = (int32_t)s9;
+        }
+        __syncthreads();
+        cta_scan(npoff, tcount, warp_sums, &s_total);
+        if (!in_bounds(g, s_total <= A.npcap)) {
+            reset_slot(posmap, qcnt, touched, P, L, tcount);
+            continue;
+        }
+        for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
+            const uint32_t b = (uint32_t)__ldcg(touched + t);
+            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
+            const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
+            int32_t base = __ldcg(npoff + t);
+            const int32_t lim = __ldcg(npoff + t + 1);
+            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            for (int64_t e0 = bu; e0 < be; e0 += 32) {
+                const int64_t e = e0 + lane;
+                const bool valid = e < be;
+                const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+                const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
+                const bool isP = valid && p >= 0;
+                const uint32_t bal = __ballot_sync(0xffffffffu, isP);
+                if (isP) {
+                    const int32_t idx = base + __popc(bal & lt);
+                    if (in_bounds(g, idx < lim)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
                 }
-                c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
-                if (lane == 0) {
-                    wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
+                base += __popc(bal);
+                if (valid && p < 0) {
+                    const uint32_t f = ent & 3u;
+                    c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
                 }
             }
-            __syncthreads();
+            c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
+            if (lane == 0) {
+                in_bounds(g, base == lim);
+                wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
+            }
         }
+        __syncthreads();
 
         // ---- phase 5: per member v of P
         for (int32_t i = warp; i < L; i += HUB_WARPS) {
@@ -429,6 +463,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     sadd(rootP, cls, (unsigned long long)pairs);
                 }
                 // -- per H-neighbour u of v
+                const int64_t dv = ve - vb;
                 for (int32_t j = lane; j < dH; j += 32) {
                     const uint32_t eu = __ldcg(hlist + h0 + j);
                     const uint32_t up = eu >> 2, fvu = eu & 3u;
@@ -447,28 +482,44 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                         sadd(hv, cls, (unsigned long long)cnt);
                         sadd(rootP, cls, (unsigned long long)cnt);
                     }
-                    // S2 credit of u as the P member not adjacent to c, with
-                    // c in NQ(v) \ N(u): |NQ(v)| - |NQ(v) n N(u)| by h(v,c)
-                    uint32_t cq[3] = {0u, 0u, 0u};
+                    // S2 across the H-edge (v,u), handled once by the endpoint of
+                    // larger degree: common Q-neighbours c of v and u
                     const int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
-                    if (ue - ub <= ve - vb) {
-                        for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r); e < ue; e++) {
-                            const uint32_t c = __ldg(g.col + e) >> 2;
-                            if (__ldcg(posmap + c) >= 0) continue;
-                            const uint32_t fvc = search_row(g.col, vu, ve, c);
-                            if (fvc) cq[fvc - 1]++;
-                        }
-                    } else {
-                        for (int64_t e = vu; e < ve; e++) {
-                            const uint32_t ec = __ldg(g.col + e);
-                            const uint32_t c = ec >> 2;
-                            if (__ldcg(posmap + c) >= 0) continue;
-                            if (search_row(g.col, ub, ue, c)) cq[(ec & 3u) - 1]++;
-                        }
+                    const int64_t du = ue - ub;
+                    if (!(dv > du || (dv == du && (uint32_t)i < up))) continue;
+                    uint32_t cqv[3] = {0u, 0u, 0u}, cqu[3] = {0u, 0u, 0u};
+                    const uint32_t fuv = swapf(fvu);
+                    // scan u's Q-neighbours (u has the smaller degree); v in NP(c)?
+                    for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r); e < ue; e++) {
+                        const uint32_t ec = __ldg(g.col + e);
+                        const uint32_t c = ec >> 2;
+                        const int32_t pc = __ldcg(posmap + c);
+                        if (pc >= 0) continue;
+                        if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                        const int64_t tc = -3 - (int64_t)pc;
+                        const uint32_t fvc = hlist_find(nplist, __ldcg(npoff + tc), __ldcg(npoff + tc + 1), (uint32_t)i);
+                        if (!fvc) continue;
+                        const uint32_t fuc = ec & 3u;
+                        cqv[fvc - 1]++;
+                        cqu[fuc - 1]++;
+                        // both adjacent to c and to each other: enumerate, and take
+                        // the pair out of c's non-adjacent-pair count
+                        const uint32_t cle = lut[mask4(al, cu, 0u, fvu, fvc, fuc)];
+                        const uint32_t clb = lut[mask4(al, cu, 0u, 0u, fvc, fuc)];
+                        sadd(hv, cle, 1ull);
+                        gadd(S, u, cle, 1ull, C);
+                        gadd(S, c, cle, 1ull, C);
+                        sadd(rootD, cle, 1ull);
+                        sadd(hv, clb, ~0ull);
+                        gadd(S, u, clb, ~0ull, C);
+                        gadd(S, c, clb, ~0ull, C);
+                        sadd(rootD, clb, ~0ull);
                     }
+                    // S2 credit of u for c in NQ(v) \ N(u) and of v for c in NQ(u) \ N(v)
                     for (uint32_t f = 1; f <= 3; f++) {
-                        const uint32_t cls = lut[mask4(al, cu, 0u, fvu, f, 0u)];
-                        gadd(S, u, cls, (unsigned long long)(Wv[f - 1] - cq[f - 1]), C);
+                        gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)(Wv[f - 1] - cqv[f - 1]), C);
+                        sadd(hv, lut[mask4(cu, al, 0u, fuv, f, 0u)],
+                             (unsigned long long)(__ldcg(wx + up * 3 + f - 1) - cqu[f - 1]));
                     }
                 }
                 // -- S1 sets with two or three H-edges, v the centre
@@ -495,8 +546,6 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 // -- Q side: lanes over c in NQ(v)
                 long long Z[9];
                 for (int k = 0; k < 9; k++) Z[k] = 0;
-                unsigned long long Tp[9];  // S3 triangle pairs by (h(v,b), h(v,c)), b < c
-                for (int k = 0; k < 9; k++) Tp[k] = 0;
                 for (int64_t e = vu + lane; e < ve; e += 32) {
                     const uint32_t ec = __ldg(g.col + e);
                     const uint32_t c = ec >> 2, f = ec & 3u;
@@ -509,29 +558,29 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                         q[k] = __ldcg(qcnt + tc * 9 + k);
                         np[k / 3] += q[k];
                     }
+                    const int32_t o0 = __ldcg(npoff + tc), o1 = __ldcg(npoff + tc + 1);
                     // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
                     uint32_t comT[9], comC[9];
                     for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
-                    const int64_t cb = __ldg(g.rowptr + c), ce = __ldg(g.rowptr + c + 1);
                     if (dH > 0) {
-                        if (ce - cb <= (int64_t)dH) {
-                            for (int64_t x = upper_row(g.col, cb, ce, (uint32_t)r); x < ce; x++) {
-                                const uint32_t ey = __ldg(g.col + x);
-                                const int32_t py = __ldcg(posmap + (ey >> 2));
-                                if (py < 0 || py == i) continue;
-                                const uint32_t fvy = hlist_find(hlist, h0, h1, (uint32_t)py);
+                        if (o1 - o0 <= dH) {
+                            for (int32_t x = o0; x < o1; x++) {
+                                const uint32_t ey = __ldcg(nplist + x);
+                                const uint32_t py = ey >> 2;
+                                if (py == (uint32_t)i) continue;
+                                const uint32_t fvy = hlist_find(hlist, h0, h1, py);
                                 if (!fvy) continue;
                                 const uint32_t cy = __ldg(P + py) & 3u;
                                 comT[(cy - 1) * 3 + fvy - 1]++;
-                                comC[(cy - 1) * 3 + swapf(ey & 3u) - 1]++;
+                                comC[(cy - 1) * 3 + (ey & 3u) - 1]++;
                             }
                         } else {
                             for (int32_t j = 0; j < dH; j++) {
                                 const uint32_t eyv = __ldcg(hlist + h0 + j);
                                 const uint32_t yp = eyv >> 2;
-                                const uint32_t y = __ldg(P + yp) >> 2, cy = __ldg(P + yp) & 3u;
-                                const uint32_t fyc = pair_flags(g, y, c);
+                                const uint32_t fyc = hlist_find(nplist, o0, o1, yp);
                                 if (!fyc) continue;
+                                const uint32_t cy = __ldg(P + yp) & 3u;
                                 comT[(cy - 1) * 3 + (eyv & 3u) - 1]++;
                                 comC[(cy - 1) * 3 + fyc - 1]++;
                             }
@@ -558,52 +607,20 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     // S2 credit of v as the P member not adjacent to c (collected in Z)
                     for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k];
                     Z[(al - 1) * 3 + f - 1] -= 1;
-                    // S3 / S4 with b = c: triangles v - c - c2, c2 in NQ(v)
-                    uint32_t T3[3] = {0u, 0u, 0u}, T4[3] = {0u, 0u, 0u};
-                    const bool scan_c = (ce - cb) <= (ve - vb);
-                    const int64_t s0 = scan_c ? upper_row(g.col, cb, ce, (uint32_t)r) : vu;
-                    const int64_t s1 = scan_c ? ce : ve;
-                    for (int64_t x = s0; x < s1; x++) {
-                        const uint32_t e2 = __ldg(g.col + x);
-                        const uint32_t c2 = e2 >> 2;
-                        if (c2 == c || __ldcg(posmap + c2) >= 0) continue;
-                        uint32_t fvc2, fcc2;
-                        if (scan_c) {
-                            fcc2 = e2 & 3u;
-                            fvc2 = search_row(g.col, vu, ve, c2);
-                        } else {
-                            fvc2 = e2 & 3u;
-                            fcc2 = search_row(g.col, cb, ce, c2);
-                        }
-                        if (!fvc2 || !fcc2) continue;
-                        T3[fvc2 - 1]++;
-                        T4[fcc2 - 1]++;
-                        const uint32_t cls3 = lut[mask4(al, 0u, 0u, f, fvc2, fcc2)];
-                        gadd(S, c, cls3, 1ull, C);
-                        if (c < c2) {
-                            sadd(hv, cls3, 1ull);
-                            sadd(rootD, cls3, 1ull);
-                            Tp[(f - 1) * 3 + fvc2 - 1]++;
-                        }
-                        const uint32_t cls4 = lut[mask4(al, 0u, 0u, f, 0u, fcc2)];
-                        gadd(S, c, cls4, ~0ull, C);   // -1: correction of the per-(c, c2) S4 count
-                        gadd(S, c2, cls4, ~0ull, C);
-                    }
                     for (uint32_t f2 = 1; f2 <= 3; f2++) {
-                        // S3 credit of c: partners in NQ(v) not adjacent to c
-                        const long long cnt3 = (long long)Wv[f2 - 1] - (f == f2) - T3[f2 - 1];
+                        // S3 credit of c: every other c2 in NQ(v) as partner
+                        // (adjacent partners are corrected per triangle)
+                        const long long cnt3 = (long long)Wv[f2 - 1] - (f == f2);
                         gadd(S, c, lut[mask4(al, 0u, 0u, f, f2, 0u)], (unsigned long long)cnt3, C);
-                        // S4 with (x, b) = (v, c): c's Q-neighbours not adjacent to v
-                        const long long cnt4 = (long long)__ldcg(wq + tc * 3 + f2 - 1) - T4[f2 - 1];
+                        // S4 with (x, b) = (v, c): every Q-neighbour of c as the
+                        // depth-3 vertex (those adjacent to v corrected per triangle)
+                        const unsigned long long cnt4 = __ldcg(wq + tc * 3 + f2 - 1);
                         const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
-                        sadd(hv, cls, (unsigned long long)cnt4);
-                        sadd(rootD, cls, (unsigned long long)cnt4);
+                        sadd(hv, cls, cnt4);
+                        sadd(rootD, cls, cnt4);
                     }
                 }
-                for (int k = 0; k < 9; k++) {
-                    Z[k] = warp_sum(Z[k]);
-                    Tp[k] = warp_sum(Tp[k]);
-                }
+                for (int k = 0; k < 9; k++) Z[k] = warp_sum(Z[k]);
                 // S2 credit of v as the non-adjacent P member (x not in N_H[v])
                 if (lane < 9) {
                     long long wsum = 0;
@@ -615,14 +632,13 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     const uint32_t cls = lut[mask4((uint32_t)(lane / 3 + 1), al, 0u, 0u, (uint32_t)(lane % 3 + 1), 0u)];
                     sadd(hv, cls, (unsigned long long)base);
                 }
-                // S3 credit of v and r: pairs {b, c} c NQ(v) by flags, minus triangles
+                // S3 credit of v and r: pairs {b, c} c NQ(v) by flags (adjacent
+                // pairs corrected per triangle)
                 if (lane < 6) {
                     const uint32_t f1 = lane < 3 ? 1u : (lane < 5 ? 2u : 3u);
                     const uint32_t f2 = lane < 3 ? (uint32_t)lane + 1 : (lane < 5 ? (uint32_t)lane - 1 : 3u);
-                    long long pairs = f1 < f2 ? (long long)Wv[f1 - 1] * Wv[f2 - 1]
-                                              : (long long)Wv[f1 - 1] * ((long long)Wv[f1 - 1] - 1) / 2;
-                    pairs -= (long long)Tp[(f1 - 1) * 3 + f2 - 1];
-                    if (f1 != f2) pairs -= (long long)Tp[(f2 - 1) * 3 + f1 - 1];
+                    const long long pairs = f1 < f2 ? (long long)Wv[f1 - 1] * Wv[f2 - 1]
+                                                    : (long long)Wv[f1 - 1] * ((long long)Wv[f1 - 1] - 1) / 2;
                     const uint32_t cls = lut[mask4(al, 0u, 0u, f1, f2, 0u)];
                     sadd(hv, cls, (unsigned long long)pairs);
                     sadd(rootD, cls, (unsigned long long)pairs);
@@ -637,69 +653,88 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
         for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
             const uint32_t b = (uint32_t)__ldcg(touched + t);
             uint32_t q[9];
-            uint32_t npb = 0;
-            for (int k = 0; k < 9; k++) {
-                q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
-                npb += q[k];
-            }
+            for (int k = 0; k < 9; k++) q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
             const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
             const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
+            const int32_t o0 = __ldcg(npoff + t), o1 = __ldcg(npoff + t + 1);
             if (K == 3) {
                 // path with b at depth 2: by (colour, flag) of its P neighbours
                 if (lane < 9) {
                     const uint32_t cls = lut[mask3((uint32_t)(lane / 3 + 1), 0u, (uint32_t)(lane % 3 + 1))];
                     gadd(S, b, cls, q[lane], C);
                 }
-            } else {
-                // S4 credit of b: P neighbours x by (colour, h(x,b)), Q neighbours by flag
-                if (lane < 27) {
-                    const int k = lane / 3, g3 = lane % 3;
-                    const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
-                    gadd(S, b, cls, (unsigned long long)q[k] * __ldcg(wq + (int64_t)t * 3 + g3), C);
+                continue;
+            }
+            // S4 credit of b: P neighbours x by (colour, h(x,b)), Q neighbours by flag
+            if (lane < 27) {
+                const int k = lane / 3, g3 = lane % 3;
+                const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
+                gadd(S, b, cls, (unsigned long long)q[k] * __ldcg(wq + (int64_t)t * 3 + g3), C);
+            }
+            // S2 with b adjacent to two members x, y of P, counted as if x, y
+            // were not adjacent (H-adjacent pairs are corrected per H-edge):
+            // pairs of NP(b) by the (colour, h(., b)) types of their members
+            for (int pr = lane; pr < 81; pr += 32) {
+                const int t1 = pr / 9, t2 = pr % 9;
+                if (t1 > t2) continue;
+                const unsigned long long cnt = t1 < t2 ? (unsigned long long)q[t1] * q[t2]
+                                                       : (unsigned long long)q[t1] * (q[t1] - (q[t1] ? 1u : 0u)) / 2;
+                const uint32_t cls = lut[mask4((uint32_t)(t1 / 3 + 1), (uint32_t)(t2 / 3 + 1), 0u, 0u,
+                                               (uint32_t)(t1 % 3 + 1), (uint32_t)(t2 % 3 + 1))];
+                gadd(S, b, cls, cnt, C);
+                sadd(rootD, cls, cnt);
+            }
+            for (int32_t x = o0 + lane; x < o1; x += 32) {
+                const uint32_t ex = __ldcg(nplist + x);
+                const uint32_t xp = ex >> 2, fxb = ex & 3u;
+                const uint32_t cx = __ldg(P + xp) & 3u;
+                const int tx = (int)((cx - 1) * 3 + fxb - 1);
+                const uint32_t xv = __ldg(P + xp) >> 2;
+                for (int k = 0; k < 9; k++) {
+                    const unsigned long long cnt = q[k] - (k == tx ? 1u : 0u);
+                    gadd(S, xv, lut[mask4(cx, (uint32_t)(k / 3 + 1), 0u, 0u, fxb, (uint32_t)(k % 3 + 1))], cnt, C);
                 }
-                // S4 credit of each c in NQ(b)
-                for (int64_t e = bu + lane; e < be; e += 32) {
-                    const uint32_t ent = __ldg(g.col + e);
-                    const uint32_t c = ent >> 2;
-                    if (__ldcg(posmap + c) >= 0) continue;
-                    const uint32_t gg = ent & 3u;
-                    for (int k = 0; k < 9; k++)
-                        if (q[k]) gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], q[k], C);
-                }
-                // S2 with b adjacent to two members x, y of P: enumerate
-                if (npb >= 2 && in_bounds(g, npb <= (uint32_t)A.lmax)) {
-                    int32_t cnt = 0;
-                    for (int64_t e0 = bu; e0 < be; e0 += 32) {
-                        const int64_t e = e0 + lane;
-                        const bool valid = e < be;
-                        const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
-                        const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
-                        const bool isP = valid && p >= 0;
-                        const uint32_t bal = __ballot_sync(0xffffffffu, isP);
-                        if (isP && cnt + __popc(bal & lt) < A.lmax)
-                            npbuf[cnt + __popc(bal & lt)] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
-                        cnt += __popc(bal);
+            }
+            // S4 credit of each c in NQ(b); triangles v - b - c2 with c2 in
+            // NQ(b), b < c2: enumerate the S3 set and correct the bulk counts
+            for (int64_t e = bu + lane; e < be; e += 32) {
+                const uint32_t ent = __ldg(g.col + e);
+                const uint32_t c = ent >> 2;
+                const int32_t pc = __ldcg(posmap + c);
+                if (pc >= 0) continue;
+                const uint32_t gg = ent & 3u;
+                for (int k = 0; k < 9; k++)
+                    if (q[k]) gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], q[k], C);
+                if (pc == -1 || c <= b) continue;  // no P neighbour, or counted from c
+                if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                const int64_t t2 = -3 - (int64_t)pc;
+                const int32_t p0 = __ldcg(npoff + t2), p1 = __ldcg(npoff + t2 + 1);
+                const bool short_b = (o1 - o0) <= (p1 - p0);
+                const int32_t s0 = short_b ? o0 : p0, s1 = short_b ? o1 : p1;
+                for (int32_t x = s0; x < s1; x++) {
+                    const uint32_t ex = __ldcg(nplist + x);
+                    const uint32_t vp = ex >> 2;
+                    const uint32_t fo = short_b ? hlist_find(nplist, p0, p1, vp) : hlist_find(nplist, o0, o1, vp);
+                    if (!fo) continue;
+                    const uint32_t fvb = short_b ? (ex & 3u) : fo;    // h(v, b)
+                    const uint32_t fvc = short_b ? fo : (ex & 3u);    // h(v, c)
+                    const uint32_t cv = __ldg(P + vp) & 3u;
+                    const uint32_t vv = __ldg(P + vp) >> 2;
+                    const uint32_t clE = lut[mask4(cv, 0u, 0u, fvb, fvc, gg)];
+                    const uint32_t clF = lut[mask4(cv, 0u, 0u, fvb, fvc, 0u)];
+                    const uint32_t clA = lut[mask4(cv, 0u, 0u, fvb, 0u, gg)];
+                    const uint32_t clB = lut[mask4(cv, 0u, 0u, fvc, 0u, swapf(gg))];
+                    const uint32_t who[3] = {vv, b, c};
+                    for (int m = 0; m < 3; m++) {
+                        gadd(S, who[m], clE, 1ull, C);
+                        gadd(S, who[m], clF, ~0ull, C);
+                        gadd(S, who[m], clA, ~0ull, C);
+                        gadd(S, who[m], clB, ~0ull, C);
                     }
-                    __syncwarp();
-                    cnt = min(cnt, (int32_t)A.lmax);
-                    for (int32_t j1 = 0; j1 < cnt; j1++) {
-                        const uint32_t e1 = __ldcg(npbuf + j1);
-                        const uint32_t xp = e1 >> 2, fxb = e1 & 3u;
-                        const uint32_t cx = __ldg(P + xp) & 3u;
-                        const int32_t x0 = __ldcg(hptr + xp), x1 = __ldcg(hptr + xp + 1);
-                        for (int32_t j2 = j1 + 1 + lane; j2 < cnt; j2 += 32) {
-                            const uint32_t e2 = __ldcg(npbuf + j2);
-                            const uint32_t yp = e2 >> 2, fyb = e2 & 3u;
-                            const uint32_t cy = __ldg(P + yp) & 3u;
-                            const uint32_t fxy = hlist_find(hlist, x0, x1, yp);
-                            const uint32_t cls = lut[mask4(cx, cy, 0u, fxy, fxb, fyb)];
-                            gadd(S, __ldg(P + xp) >> 2, cls, 1ull, C);
-                            gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
-                            gadd(S, b, cls, 1ull, C);
-                            sadd(rootD, cls, 1ull);
-                        }
-                    }
-                    __syncwarp();
+                    sadd(rootD, clE, 1ull);
+                    sadd(rootD, clF, ~0ull);
+                    sadd(rootD, clA, ~0ull);
+                    sadd(rootD, clB, ~0ull);
                 }
             }
         }
@@ -713,11 +748,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
             }
         }
-        for (int32_t p = tid; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
-        for (int32_t t = tid; t < tcount; t += HUB_THREADS) {
-            posmap[__ldcg(touched + t)] = -1;
-            for (int k = 0; k < 9; k++) qcnt[(int64_t)t * 9 + k] = 0u;
-        }
+        reset_slot(posmap, qcnt, touched, P, L, tcount);
     }
 }
 
@@ -820,6 +851,7 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
         g->hub_lmax = (int64_t)h[0];
         g->hub_hcap = std::max<int64_t>(1, (int64_t)h[1]);
         g->hub_tcap = std::max<int64_t>(1, std::min<int64_t>((int64_t)n, (int64_t)h[2]));
+        g->hub_npcap = std::max<int64_t>(1, std::min<int64_t>((int64_t)0x7fffffff, (int64_t)h[2]));
         g->nhubs = (int32_t)nh;
     }
     cudaFreeAsync(flag, s);
@@ -832,7 +864,7 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
 namespace {
 
 struct HubLayout {
-    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npbuf, total;
+    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npoff, nplist, total;
 };
 
 HubLayout hub_layout(const vdmc_graph *g, int slots) {
@@ -848,7 +880,8 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
     L.hcx = o; o += align256(S * lm * 3 * 4);
     L.wx = o; o += align256(S * lm * 3 * 4);
     L.htx = o; o += align256(S * lm * 9 * 4);
-    L.npbuf = o; o += align256(S * HUB_WARPS * lm * 4);
+    L.npoff = o; o += align256(S * (t + 1) * 4);
+    L.nplist = o; o += align256(S * (size_t)g->hub_npcap * 4);
     L.total = o;
     return L;
 }
@@ -905,7 +938,9 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *
     A.hcx = (uint32_t *)(base + L.hcx);
     A.wx = (uint32_t *)(base + L.wx);
     A.htx = (uint32_t *)(base + L.htx);
-    A.npbuf = (uint32_t *)(base + L.npbuf);
+    A.npoff = (int32_t *)(base + L.npoff);
+    A.nplist = (uint32_t *)(base + L.nplist);
+    A.npcap = g->hub_npcap;
     A.tcap = g->hub_tcap;
     A.hcap = g->hub_hcap;
     A.lmax = g->hub_lmax;

@@ -51,7 +51,7 @@ struct vdmc_graph {
     int32_t *hubs;               // ranks of the roots it handles, heavy first
     int32_t nhubs;
     int32_t hub_min_l;
-    int64_t hub_lmax, hub_hcap, hub_tcap;
+    int64_t hub_lmax, hub_hcap, hub_tcap, hub_npcap;
     int hub_slots;
     void *hub_scratch;
     size_t hub_scratch_bytes;
