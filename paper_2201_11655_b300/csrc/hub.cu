@@ -48,7 +48,7 @@
 
 namespace {
 
-constexpr int HUB_WARPS = 8;
+constexpr int HUB_WARPS = 16;
 constexpr int HUB_THREADS = HUB_WARPS * 32;
 constexpr int32_t CLAIMED = -2;  // posmap: claimed, index being written
 
@@ -94,12 +94,12 @@ __device__ __forceinline__ uint32_t hlist_find(const uint32_t *hl, int32_t lo, i
     int32_t a = lo, b = hi;
     while (a < b) {
         int32_t mid = (a + b) >> 1;
-        uint32_t e = __ldcg(hl + mid);
+        uint32_t e = hl[mid];
         if ((e >> 2) < pos) a = mid + 1;
         else b = mid;
     }
     if (a < hi) {
-        uint32_t e = __ldcg(hl + a);
+        uint32_t e = hl[a];
         if ((e >> 2) == pos) return e & 3u;
     }
     return 0u;
@@ -130,7 +130,7 @@ __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *
     const int32_t chunk = (L + HUB_THREADS - 1) / HUB_THREADS;
     const int32_t beg = min(L, tid * chunk), end = min(L, beg + chunk);
     int32_t s = 0;
-    for (int32_t p = beg; p < end; p++) s += __ldcg(hptr + p);
+    for (int32_t p = beg; p < end; p++) s += hptr[p];
     int32_t inc = s;
     for (int o = 1; o < 32; o <<= 1) {
         int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -150,7 +150,7 @@ __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *
     __syncthreads();
     int32_t run = warp_sums[warp] + inc - s;
     for (int32_t p = beg; p < end; p++) {
-        int32_t d = __ldcg(hptr + p);
+        int32_t d = hptr[p];
         hptr[p] = run;
         run += d;
     }
@@ -164,7 +164,7 @@ __device__ void reset_slot(int32_t *posmap, uint32_t *qcnt, const int32_t *touch
                            int32_t tcount) {
     for (int32_t p = threadIdx.x; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
     for (int32_t t = threadIdx.x; t < tcount; t += HUB_THREADS) {
-        posmap[__ldcg(touched + t)] = -1;
+        posmap[touched[t]] = -1;
         for (int k = 0; k < 9; k++) qcnt[(int64_t)t * 9 + k] = 0u;
     }
 }
@@ -176,7 +176,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
+__global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args) {
     constexpr int C = (K == 3) ? 13 : 199;
     constexpr int NIDX = 1 << (K * (K - 1));
     __shared__ uint8_t lut[NIDX];
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
             const uint32_t x = ex >> 2, fx = ex & 3u;
             const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
             const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
-            int32_t base = __ldcg(hptr + i);
+            int32_t base = hptr[i];
             uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
             for (int64_t e0 = xu; e0 < xe; e0 += 32) {
                 const int64_t e = e0 + lane;
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 uint32_t *h9 = htx + (int64_t)i * 9;
                 h9[0] = t0; h9[1] = t1; h9[2] = t2; h9[3] = t3; h9[4] = t4;
                 h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
-                for (int f = 0; f < 3; f++) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)__ldcg(wx + i * 3 + f));
+                for (int f = 0; f < 3; f++) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)wx[i * 3 + f]);
             }
         }
         __syncthreads();
@@ -348,11 +348,11 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
             continue;
         }
         for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
-            const uint32_t b = (uint32_t)__ldcg(touched + t);
+            const uint32_t b = (uint32_t)touched[t];
             const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
             const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-            int32_t base = __ldcg(npoff + t);
-            const int32_t lim = __ldcg(npoff + t + 1);
+            int32_t base = npoff[t];
+            const int32_t lim = npoff[t + 1];
             uint32_t c0 = 0, c1 = 0, c2 = 0;
             for (int64_t e0 = bu; e0 < be; e0 += 32) {
                 const int64_t e = e0 + lane;
@@ -383,12 +383,12 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
         for (int32_t i = warp; i < L; i += HUB_WARPS) {
             const uint32_t ev = __ldg(P + i);
             const uint32_t v = ev >> 2, al = ev & 3u;
-            const int32_t h0 = __ldcg(hptr + i), h1 = __ldcg(hptr + i + 1);
+            const int32_t h0 = hptr[i], h1 = hptr[i + 1];
             const int32_t dH = h1 - h0;
             uint32_t hcv[3], Wv[3];
             for (int k = 0; k < 3; k++) {
-                hcv[k] = __ldcg(hcx + i * 3 + k);
-                Wv[k] = __ldcg(wx + i * 3 + k);
+                hcv[k] = hcx[i * 3 + k];
+                Wv[k] = wx[i * 3 + k];
             }
             const int64_t vb = __ldg(g.rowptr + v), ve = __ldg(g.rowptr + v + 1);
             const int64_t vu = upper_row(g.col, vb, ve, (uint32_t)r);
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     sadd(rootD, cls2, Wv[lane]);
                 }
                 for (int32_t j = lane; j < dH; j += 32) {
-                    const uint32_t eu = __ldcg(hlist + h0 + j);
+                    const uint32_t eu = hlist[h0 + j];
                     const uint32_t cu = __ldg(P + (eu >> 2)) & 3u;
                     const uint32_t cls = lut[mask3(al, cu, eu & 3u)];
                     sadd(hv, cls, 1ull);
@@ -420,19 +420,28 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     eins[warp][k] = 0u;
                 }
                 __syncwarp();
-                for (int32_t j = lane - 1; j < dH; j += 32) {
-                    const uint32_t up = j < 0 ? (uint32_t)i : (__ldcg(hlist + h0 + j) >> 2);
-                    const uint32_t cu = __ldg(P + up) & 3u;
-                    const int32_t u0 = __ldcg(hptr + up), u1 = __ldcg(hptr + up + 1);
-                    for (int32_t k = u0; k < u1; k++) {
-                        const uint32_t ew = __ldcg(hlist + k);
-                        const uint32_t w = ew >> 2;
-                        const int t = etype(cu, __ldg(P + w) & 3u, ew & 3u);
-                        atomicAdd(&esub[warp][t], 1u);
-                        if (up < w) {
-                            const bool inside = (up == (uint32_t)i) || (w == (uint32_t)i) ||
-                                                hlist_find(hlist, h0, h1, w) != 0u;
-                            if (inside) atomicAdd(&eins[warp][t], 1u);
+                // light H-neighbours (short H-lists): one per lane; heavy ones:
+                // the whole warp walks the list
+                for (int pass = 0; pass < 2; pass++) {
+                    const int32_t jstart = pass == 0 ? lane - 1 : -1;
+                    const int32_t jstep = pass == 0 ? 32 : 1;
+                    for (int32_t j = jstart; j < dH; j += jstep) {
+                        const uint32_t up = j < 0 ? (uint32_t)i : (hlist[h0 + j] >> 2);
+                        const int32_t u0 = hptr[up], u1 = hptr[up + 1];
+                        const bool heavy = (u1 - u0) > 32;
+                        if (heavy != (pass == 1)) continue;
+                        const uint32_t cu = __ldg(P + up) & 3u;
+                        const int32_t k0 = pass == 0 ? u0 : u0 + lane, ks = pass == 0 ? 1 : 32;
+                        for (int32_t k = k0; k < u1; k += ks) {
+                            const uint32_t ew = hlist[k];
+                            const uint32_t w = ew >> 2;
+                            const int t = etype(cu, __ldg(P + w) & 3u, ew & 3u);
+                            atomicAdd(&esub[warp][t], 1u);
+                            if (up < w) {
+                                const bool inside = (up == (uint32_t)i) || (w == (uint32_t)i) ||
+                                                    hlist_find(hlist, h0, h1, w) != 0u;
+                                if (inside) atomicAdd(&eins[warp][t], 1u);
+                            }
                         }
                     }
                 }
@@ -462,74 +471,96 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                     sadd(hv, cls, (unsigned long long)pairs);
                     sadd(rootP, cls, (unsigned long long)pairs);
                 }
-                // -- per H-neighbour u of v
+                // -- per H-neighbour u of v (light u: one per lane; heavy u: the
+                // whole warp shares its lists)
                 const int64_t dv = ve - vb;
-                for (int32_t j = lane; j < dH; j += 32) {
-                    const uint32_t eu = __ldcg(hlist + h0 + j);
-                    const uint32_t up = eu >> 2, fvu = eu & 3u;
-                    const uint32_t u = __ldg(P + up) >> 2, cu = __ldg(P + up) & 3u;
-                    const int32_t u0 = __ldcg(hptr + up), u1 = __ldcg(hptr + up + 1);
-                    uint32_t com[3] = {0u, 0u, 0u};
-                    for (int32_t k = u0; k < u1; k++) {
-                        const uint32_t w = __ldcg(hlist + k) >> 2;
-                        if (w != (uint32_t)i && hlist_find(hlist, h0, h1, w)) com[(__ldg(P + w) & 3u) - 1]++;
-                    }
-                    // S1 one H-edge (v,u), third member isolated, by its colour
-                    for (uint32_t ga = 1; ga <= 3; ga++) {
-                        const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - __ldcg(hcx + up * 3 + ga - 1) +
-                                              com[ga - 1];
-                        const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
-                        sadd(hv, cls, (unsigned long long)cnt);
-                        sadd(rootP, cls, (unsigned long long)cnt);
-                    }
-                    // S2 across the H-edge (v,u), handled once by the endpoint of
-                    // larger degree: common Q-neighbours c of v and u
-                    const int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
-                    const int64_t du = ue - ub;
-                    if (!(dv > du || (dv == du && (uint32_t)i < up))) continue;
-                    uint32_t cqv[3] = {0u, 0u, 0u}, cqu[3] = {0u, 0u, 0u};
-                    const uint32_t fuv = swapf(fvu);
-                    // scan u's Q-neighbours (u has the smaller degree); v in NP(c)?
-                    for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r); e < ue; e++) {
-                        const uint32_t ec = __ldg(g.col + e);
-                        const uint32_t c = ec >> 2;
-                        const int32_t pc = __ldcg(posmap + c);
-                        if (pc >= 0) continue;
-                        if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
-                        const int64_t tc = -3 - (int64_t)pc;
-                        const uint32_t fvc = hlist_find(nplist, __ldcg(npoff + tc), __ldcg(npoff + tc + 1), (uint32_t)i);
-                        if (!fvc) continue;
-                        const uint32_t fuc = ec & 3u;
-                        cqv[fvc - 1]++;
-                        cqu[fuc - 1]++;
-                        // both adjacent to c and to each other: enumerate, and take
-                        // the pair out of c's non-adjacent-pair count
-                        const uint32_t cle = lut[mask4(al, cu, 0u, fvu, fvc, fuc)];
-                        const uint32_t clb = lut[mask4(al, cu, 0u, 0u, fvc, fuc)];
-                        sadd(hv, cle, 1ull);
-                        gadd(S, u, cle, 1ull, C);
-                        gadd(S, c, cle, 1ull, C);
-                        sadd(rootD, cle, 1ull);
-                        sadd(hv, clb, ~0ull);
-                        gadd(S, u, clb, ~0ull, C);
-                        gadd(S, c, clb, ~0ull, C);
-                        sadd(rootD, clb, ~0ull);
-                    }
-                    // S2 credit of u for c in NQ(v) \ N(u) and of v for c in NQ(u) \ N(v)
-                    for (uint32_t f = 1; f <= 3; f++) {
-                        gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)(Wv[f - 1] - cqv[f - 1]), C);
-                        sadd(hv, lut[mask4(cu, al, 0u, fuv, f, 0u)],
-                             (unsigned long long)(__ldcg(wx + up * 3 + f - 1) - cqu[f - 1]));
+                for (int pass = 0; pass < 2; pass++) {
+                    const int32_t jstart = pass == 0 ? lane : 0, jstep = pass == 0 ? 32 : 1;
+                    for (int32_t j = jstart; j < dH; j += jstep) {
+                        const uint32_t eu = hlist[h0 + j];
+                        const uint32_t up = eu >> 2, fvu = eu & 3u;
+                        const uint32_t u = __ldg(P + up) >> 2, cu = __ldg(P + up) & 3u;
+                        const int32_t u0 = hptr[up], u1 = hptr[up + 1];
+                        const int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
+                        const int64_t du = ue - ub;
+                        const bool heavy = (u1 - u0) > 32 || du > 64;
+                        if (heavy != (pass == 1)) continue;
+                        const bool coop = pass == 1;
+                        const int32_t ls = coop ? lane : 0, st = coop ? 32 : 1;
+                        uint32_t com0 = 0, com1 = 0, com2 = 0;
+                        for (int32_t k = u0 + ls; k < u1; k += st) {
+                            const uint32_t w = hlist[k] >> 2;
+                            if (w != (uint32_t)i && hlist_find(hlist, h0, h1, w)) {
+                                const uint32_t cw = __ldg(P + w) & 3u;
+                                com0 += cw == 1u; com1 += cw == 2u; com2 += cw == 3u;
+                            }
+                        }
+                        if (coop) {
+                            com0 = warp_sum(com0); com1 = warp_sum(com1); com2 = warp_sum(com2);
+                        }
+                        const uint32_t com[3] = {com0, com1, com2};
+                        // S1 one H-edge (v,u), third member isolated, by its colour
+                        if (!coop || lane == 0) {
+                            for (uint32_t ga = 1; ga <= 3; ga++) {
+                                const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - hcx[up * 3 + ga - 1] + com[ga - 1];
+                                const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
+                                sadd(hv, cls, (unsigned long long)cnt);
+                                sadd(rootP, cls, (unsigned long long)cnt);
+                            }
+                        }
+                        // S2 across the H-edge (v,u), handled once by the endpoint of
+                        // larger degree: common Q-neighbours c of v and u
+                        if (!(dv > du || (dv == du && (uint32_t)i < up))) continue;
+                        uint32_t cqv0 = 0, cqv1 = 0, cqv2 = 0, cqu0 = 0, cqu1 = 0, cqu2 = 0;
+                        const uint32_t fuv = swapf(fvu);
+                        // scan u's Q-neighbours (u has the smaller degree); v in NP(c)?
+                        for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r) + ls; e < ue; e += st) {
+                            const uint32_t ec = __ldg(g.col + e);
+                            const uint32_t c = ec >> 2;
+                            const int32_t pc = __ldcg(posmap + c);
+                            if (pc >= 0) continue;
+                            if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                            const int64_t tc = -3 - (int64_t)pc;
+                            const uint32_t fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
+                            if (!fvc) continue;
+                            const uint32_t fuc = ec & 3u;
+                            cqv0 += fvc == 1u; cqv1 += fvc == 2u; cqv2 += fvc == 3u;
+                            cqu0 += fuc == 1u; cqu1 += fuc == 2u; cqu2 += fuc == 3u;
+                            // both adjacent to c and to each other: enumerate, and take
+                            // the pair out of c's non-adjacent-pair count
+                            const uint32_t cle = lut[mask4(al, cu, 0u, fvu, fvc, fuc)];
+                            const uint32_t clb = lut[mask4(al, cu, 0u, 0u, fvc, fuc)];
+                            sadd(hv, cle, 1ull);
+                            gadd(S, u, cle, 1ull, C);
+                            gadd(S, c, cle, 1ull, C);
+                            sadd(rootD, cle, 1ull);
+                            sadd(hv, clb, ~0ull);
+                            gadd(S, u, clb, ~0ull, C);
+                            gadd(S, c, clb, ~0ull, C);
+                            sadd(rootD, clb, ~0ull);
+                        }
+                        if (coop) {
+                            cqv0 = warp_sum(cqv0); cqv1 = warp_sum(cqv1); cqv2 = warp_sum(cqv2);
+                            cqu0 = warp_sum(cqu0); cqu1 = warp_sum(cqu1); cqu2 = warp_sum(cqu2);
+                        }
+                        const uint32_t cqv[3] = {cqv0, cqv1, cqv2}, cqu[3] = {cqu0, cqu1, cqu2};
+                        // S2 credit of u for c in NQ(v) \ N(u) and of v for c in NQ(u) \ N(v)
+                        if (!coop || lane == 0) {
+                            for (uint32_t f = 1; f <= 3; f++) {
+                                gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)(Wv[f - 1] - cqv[f - 1]), C);
+                                sadd(hv, lut[mask4(cu, al, 0u, fuv, f, 0u)], (unsigned long long)(wx[up * 3 + f - 1] - cqu[f - 1]));
+                            }
+                        }
                     }
                 }
                 // -- S1 sets with two or three H-edges, v the centre
                 for (int32_t j1 = 0; j1 < dH; j1++) {
-                    const uint32_t e1 = __ldcg(hlist + h0 + j1);
+                    const uint32_t e1 = hlist[h0 + j1];
                     const uint32_t yp = e1 >> 2, fvy = e1 & 3u;
                     const uint32_t cy = __ldg(P + yp) & 3u;
-                    const int32_t y0 = __ldcg(hptr + yp), y1 = __ldcg(hptr + yp + 1);
+                    const int32_t y0 = hptr[yp], y1 = hptr[yp + 1];
                     for (int32_t j2 = j1 + 1 + lane; j2 < dH; j2 += 32) {
-                        const uint32_t e2 = __ldcg(hlist + h0 + j2);
+                        const uint32_t e2 = hlist[h0 + j2];
                         const uint32_t zp = e2 >> 2, fvz = e2 & 3u;
                         const uint32_t cz = __ldg(P + zp) & 3u;
                         const uint32_t fyz = hlist_find(hlist, y0, y1, zp);
@@ -558,14 +589,14 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                         q[k] = __ldcg(qcnt + tc * 9 + k);
                         np[k / 3] += q[k];
                     }
-                    const int32_t o0 = __ldcg(npoff + tc), o1 = __ldcg(npoff + tc + 1);
+                    const int32_t o0 = npoff[tc], o1 = npoff[tc + 1];
                     // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
                     uint32_t comT[9], comC[9];
                     for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
                     if (dH > 0) {
                         if (o1 - o0 <= dH) {
                             for (int32_t x = o0; x < o1; x++) {
-                                const uint32_t ey = __ldcg(nplist + x);
+                                const uint32_t ey = nplist[x];
                                 const uint32_t py = ey >> 2;
                                 if (py == (uint32_t)i) continue;
                                 const uint32_t fvy = hlist_find(hlist, h0, h1, py);
@@ -576,7 +607,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                             }
                         } else {
                             for (int32_t j = 0; j < dH; j++) {
-                                const uint32_t eyv = __ldcg(hlist + h0 + j);
+                                const uint32_t eyv = hlist[h0 + j];
                                 const uint32_t yp = eyv >> 2;
                                 const uint32_t fyc = hlist_find(nplist, o0, o1, yp);
                                 if (!fyc) continue;
@@ -592,7 +623,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                         for (uint32_t fy = 1; fy <= 3; fy++) {
                             const uint32_t k = (be - 1) * 3 + fy - 1;
                             combe += comT[k];
-                            const long long cnt = (long long)__ldcg(htx + (int64_t)i * 9 + k) - comT[k];
+                            const long long cnt = (long long)htx[(int64_t)i * 9 + k] - comT[k];
                             const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
                             sadd(hv, cls, (unsigned long long)cnt);
                             gadd(S, c, cls, (unsigned long long)cnt, C);
@@ -614,7 +645,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                         gadd(S, c, lut[mask4(al, 0u, 0u, f, f2, 0u)], (unsigned long long)cnt3, C);
                         // S4 with (x, b) = (v, c): every Q-neighbour of c as the
                         // depth-3 vertex (those adjacent to v corrected per triangle)
-                        const unsigned long long cnt4 = __ldcg(wq + tc * 3 + f2 - 1);
+                        const unsigned long long cnt4 = wq[tc * 3 + f2 - 1];
                         const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
                         sadd(hv, cls, cnt4);
                         sadd(rootD, cls, cnt4);
@@ -625,8 +656,8 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 if (lane < 9) {
                     long long wsum = 0;
                     for (int32_t j = -1; j < dH; j++) {
-                        const uint32_t xp = j < 0 ? (uint32_t)i : (__ldcg(hlist + h0 + j) >> 2);
-                        if ((__ldg(P + xp) & 3u) == (uint32_t)(lane / 3 + 1)) wsum += __ldcg(wx + xp * 3 + lane % 3);
+                        const uint32_t xp = j < 0 ? (uint32_t)i : (hlist[h0 + j] >> 2);
+                        if ((__ldg(P + xp) & 3u) == (uint32_t)(lane / 3 + 1)) wsum += wx[xp * 3 + lane % 3];
                     }
                     const long long base = (long long)Wtot[lane] - wsum - Z[lane];
                     const uint32_t cls = lut[mask4((uint32_t)(lane / 3 + 1), al, 0u, 0u, (uint32_t)(lane % 3 + 1), 0u)];
@@ -651,12 +682,12 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
 
         // ---- phase 6: per Q vertex b
         for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
-            const uint32_t b = (uint32_t)__ldcg(touched + t);
+            const uint32_t b = (uint32_t)touched[t];
             uint32_t q[9];
             for (int k = 0; k < 9; k++) q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
             const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
             const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-            const int32_t o0 = __ldcg(npoff + t), o1 = __ldcg(npoff + t + 1);
+            const int32_t o0 = npoff[t], o1 = npoff[t + 1];
             if (K == 3) {
                 // path with b at depth 2: by (colour, flag) of its P neighbours
                 if (lane < 9) {
@@ -669,7 +700,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
             if (lane < 27) {
                 const int k = lane / 3, g3 = lane % 3;
                 const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
-                gadd(S, b, cls, (unsigned long long)q[k] * __ldcg(wq + (int64_t)t * 3 + g3), C);
+                gadd(S, b, cls, (unsigned long long)q[k] * wq[(int64_t)t * 3 + g3], C);
             }
             // S2 with b adjacent to two members x, y of P, counted as if x, y
             // were not adjacent (H-adjacent pairs are corrected per H-edge):
@@ -685,7 +716,7 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 sadd(rootD, cls, cnt);
             }
             for (int32_t x = o0 + lane; x < o1; x += 32) {
-                const uint32_t ex = __ldcg(nplist + x);
+                const uint32_t ex = nplist[x];
                 const uint32_t xp = ex >> 2, fxb = ex & 3u;
                 const uint32_t cx = __ldg(P + xp) & 3u;
                 const int tx = (int)((cx - 1) * 3 + fxb - 1);
@@ -708,11 +739,11 @@ __global__ void __launch_bounds__(HUB_THREADS) hub_kernel(const HubArgs args) {
                 if (pc == -1 || c <= b) continue;  // no P neighbour, or counted from c
                 if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
                 const int64_t t2 = -3 - (int64_t)pc;
-                const int32_t p0 = __ldcg(npoff + t2), p1 = __ldcg(npoff + t2 + 1);
+                const int32_t p0 = npoff[t2], p1 = npoff[t2 + 1];
                 const bool short_b = (o1 - o0) <= (p1 - p0);
                 const int32_t s0 = short_b ? o0 : p0, s1 = short_b ? o1 : p1;
                 for (int32_t x = s0; x < s1; x++) {
-                    const uint32_t ex = __ldcg(nplist + x);
+                    const uint32_t ex = nplist[x];
                     const uint32_t vp = ex >> 2;
                     const uint32_t fo = short_b ? hlist_find(nplist, p0, p1, vp) : hlist_find(nplist, o0, o1, vp);
                     if (!fo) continue;
