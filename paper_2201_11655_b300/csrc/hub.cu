@@ -245,41 +245,48 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
 
         // ---- phase 2: per x in P: |NH(x)|, colours of NH(x), |NQ(x)| by flag;
         // claim the Q vertices (compact index per Q vertex)
-        for (int32_t i = warp; i < L; i += HUB_WARPS) {
-            const uint32_t x = __ldg(P + i) >> 2;
-            const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
-            const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
-            uint32_t dh = 0, hc0 = 0, hc1 = 0, hc2 = 0, w0 = 0, w1 = 0, w2 = 0;
-            for (int64_t e = xu + lane; e < xe; e += 32) {
-                const uint32_t ent = __ldg(g.col + e);
-                const uint32_t u = ent >> 2, f = ent & 3u;
-                const int32_t p = __ldcg(posmap + u);
-                if (p >= 0) {
-                    dh++;
-                    const uint32_t cu = __ldg(P + p) & 3u;
-                    hc0 += cu == 1u;
-                    hc1 += cu == 2u;
-                    hc2 += cu == 3u;
-                } else {
-                    w0 += f == 1u;
-                    w1 += f == 2u;
-                    w2 += f == 3u;
-                    if (p == -1 && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
-                        const int32_t t = atomicAdd(&s_tcount, 1);
-                        if (in_bounds(g, t < A.tcap)) {
-                            touched[t] = (int32_t)u;
-                            posmap[u] = -3 - t;
+        // light x (short rows): one per thread; heavy x: one per warp
+        for (int pass = 0; pass < 2; pass++) {
+            const bool coop = pass == 1;
+            for (int32_t i = coop ? warp : tid; i < L; i += coop ? HUB_WARPS : HUB_THREADS) {
+                const uint32_t x = __ldg(P + i) >> 2;
+                const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
+                if ((xe - xb > 32) != coop) continue;
+                const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
+                uint32_t dh = 0, hc0 = 0, hc1 = 0, hc2 = 0, w0 = 0, w1 = 0, w2 = 0;
+                for (int64_t e = xu + (coop ? lane : 0); e < xe; e += coop ? 32 : 1) {
+                    const uint32_t ent = __ldg(g.col + e);
+                    const uint32_t u = ent >> 2, f = ent & 3u;
+                    const int32_t p = __ldcg(posmap + u);
+                    if (p >= 0) {
+                        dh++;
+                        const uint32_t cu = __ldg(P + p) & 3u;
+                        hc0 += cu == 1u;
+                        hc1 += cu == 2u;
+                        hc2 += cu == 3u;
+                    } else {
+                        w0 += f == 1u;
+                        w1 += f == 2u;
+                        w2 += f == 3u;
+                        if (p == -1 && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
+                            const int32_t t = atomicAdd(&s_tcount, 1);
+                            if (in_bounds(g, t < A.tcap)) {
+                                touched[t] = (int32_t)u;
+                                posmap[u] = -3 - t;
+                            }
                         }
                     }
                 }
-            }
-            dh = warp_sum(dh);
-            hc0 = warp_sum(hc0); hc1 = warp_sum(hc1); hc2 = warp_sum(hc2);
-            w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
-            if (lane == 0) {
-                hptr[i] = (int32_t)dh;
-                hcx[i * 3 + 0] = hc0; hcx[i * 3 + 1] = hc1; hcx[i * 3 + 2] = hc2;
-                wx[i * 3 + 0] = w0; wx[i * 3 + 1] = w1; wx[i * 3 + 2] = w2;
+                if (coop) {
+                    dh = warp_sum(dh);
+                    hc0 = warp_sum(hc0); hc1 = warp_sum(hc1); hc2 = warp_sum(hc2);
+                    w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+                }
+                if (!coop || lane == 0) {
+                    hptr[i] = (int32_t)dh;
+                    hcx[i * 3 + 0] = hc0; hcx[i * 3 + 1] = hc1; hcx[i * 3 + 2] = hc2;
+                    wx[i * 3 + 0] = w0; wx[i * 3 + 1] = w1; wx[i * 3 + 2] = w2;
+                }
             }
         }
         __syncthreads();
@@ -295,41 +302,50 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         }
 
         // ---- phase 3: H adjacency lists, H-edge types, per-Q-vertex P counts
-        for (int32_t i = warp; i < L; i += HUB_WARPS) {
-            const uint32_t ex = __ldg(P + i);
-            const uint32_t x = ex >> 2, fx = ex & 3u;
-            const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
-            const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
-            int32_t base = hptr[i];
-            uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
-            for (int64_t e0 = xu; e0 < xe; e0 += 32) {
-                const int64_t e = e0 + lane;
-                const bool valid = e < xe;
-                const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
-                const uint32_t u = ent >> 2, f = ent & 3u;
-                const int32_t p = valid ? __ldcg(posmap + u) : -1;
-                const bool isH = valid && p >= 0;
-                const uint32_t bal = __ballot_sync(0xffffffffu, isH);
-                if (isH) {
-                    hlist[base + __popc(bal & lt)] = ((uint32_t)p << 2) | f;
-                    const uint32_t cu = __ldg(P + p) & 3u;
-                    const uint32_t k9 = (cu - 1) * 3 + (f - 1);
-                    t0 += k9 == 0; t1 += k9 == 1; t2 += k9 == 2; t3 += k9 == 3; t4 += k9 == 4;
-                    t5 += k9 == 5; t6 += k9 == 6; t7 += k9 == 7; t8 += k9 == 8;
-                    if (i < p) atomicAdd(&Etype[etype(fx, cu, f)], 1ull);
-                } else if (valid && p <= -3) {
-                    const int64_t t = -3 - (int64_t)p;
-                    atomicAdd(qcnt + t * 9 + (fx - 1) * 3 + (f - 1), 1u);
+        for (int pass = 0; pass < 2; pass++) {
+            const bool coop = pass == 1;
+            for (int32_t i = coop ? warp : tid; i < L; i += coop ? HUB_WARPS : HUB_THREADS) {
+                const uint32_t ex = __ldg(P + i);
+                const uint32_t x = ex >> 2, fx = ex & 3u;
+                const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
+                if ((xe - xb > 32) != coop) continue;
+                const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
+                int32_t base = hptr[i];
+                uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+                for (int64_t e0 = xu; e0 < xe; e0 += coop ? 32 : 1) {
+                    const int64_t e = e0 + (coop ? lane : 0);
+                    const bool valid = e < xe;
+                    const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+                    const uint32_t u = ent >> 2, f = ent & 3u;
+                    const int32_t p = valid ? __ldcg(posmap + u) : -1;
+                    const bool isH = valid && p >= 0;
+                    const uint32_t bal = coop ? __ballot_sync(0xffffffffu, isH) : (isH ? 1u : 0u);
+                    if (isH) {
+                        hlist[base + (coop ? __popc(bal & lt) : 0)] = ((uint32_t)p << 2) | f;
+                        const uint32_t cu = __ldg(P + p) & 3u;
+                        const uint32_t k9 = (cu - 1) * 3 + (f - 1);
+                        t0 += k9 == 0; t1 += k9 == 1; t2 += k9 == 2; t3 += k9 == 3; t4 += k9 == 4;
+                        t5 += k9 == 5; t6 += k9 == 6; t7 += k9 == 7; t8 += k9 == 8;
+                        if (i < p) atomicAdd(&Etype[etype(fx, cu, f)], 1ull);
+                    } else if (valid && p <= -3) {
+                        const int64_t t = -3 - (int64_t)p;
+                        atomicAdd(qcnt + t * 9 + (fx - 1) * 3 + (f - 1), 1u);
+                    }
+                    base += __popc(bal);
                 }
-                base += __popc(bal);
-            }
-            t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2); t3 = warp_sum(t3); t4 = warp_sum(t4);
-            t5 = warp_sum(t5); t6 = warp_sum(t6); t7 = warp_sum(t7); t8 = warp_sum(t8);
-            if (lane == 0) {
-                uint32_t *h9 = htx + (int64_t)i * 9;
-                h9[0] = t0; h9[1] = t1; h9[2] = t2; h9[3] = t3; h9[4] = t4;
-                h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
-                for (int f = 0; f < 3; f++) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)wx[i * 3 + f]);
+                if (coop) {
+                    t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2); t3 = warp_sum(t3); t4 = warp_sum(t4);
+                    t5 = warp_sum(t5); t6 = warp_sum(t6); t7 = warp_sum(t7); t8 = warp_sum(t8);
+                }
+                if (!coop || lane == 0) {
+                    uint32_t *h9 = htx + (int64_t)i * 9;
+                    h9[0] = t0; h9[1] = t1; h9[2] = t2; h9[3] = t3; h9[4] = t4;
+                    h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
+                    for (int f = 0; f < 3; f++) {
+                        const uint32_t w = wx[i * 3 + f];
+                        if (w) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)w);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -347,34 +363,40 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             reset_slot(posmap, qcnt, touched, P, L, tcount);
             continue;
         }
-        for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
-            const uint32_t b = (uint32_t)touched[t];
-            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
-            const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-            int32_t base = npoff[t];
-            const int32_t lim = npoff[t + 1];
-            uint32_t c0 = 0, c1 = 0, c2 = 0;
-            for (int64_t e0 = bu; e0 < be; e0 += 32) {
-                const int64_t e = e0 + lane;
-                const bool valid = e < be;
-                const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
-                const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
-                const bool isP = valid && p >= 0;
-                const uint32_t bal = __ballot_sync(0xffffffffu, isP);
-                if (isP) {
-                    const int32_t idx = base + __popc(bal & lt);
-                    if (in_bounds(g, idx < lim)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
+        for (int pass = 0; pass < 2; pass++) {
+            const bool coop = pass == 1;
+            for (int32_t t = coop ? warp : tid; t < tcount; t += coop ? HUB_WARPS : HUB_THREADS) {
+                const uint32_t b = (uint32_t)touched[t];
+                const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
+                if ((be - bb > 32) != coop) continue;
+                const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
+                int32_t base = npoff[t];
+                const int32_t lim = npoff[t + 1];
+                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                for (int64_t e0 = bu; e0 < be; e0 += coop ? 32 : 1) {
+                    const int64_t e = e0 + (coop ? lane : 0);
+                    const bool valid = e < be;
+                    const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+                    const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
+                    const bool isP = valid && p >= 0;
+                    const uint32_t bal = coop ? __ballot_sync(0xffffffffu, isP) : (isP ? 1u : 0u);
+                    if (isP) {
+                        const int32_t idx = base + (coop ? __popc(bal & lt) : 0);
+                        if (in_bounds(g, idx < lim)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
+                    }
+                    base += __popc(bal);
+                    if (valid && p < 0) {
+                        const uint32_t f = ent & 3u;
+                        c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
+                    }
                 }
-                base += __popc(bal);
-                if (valid && p < 0) {
-                    const uint32_t f = ent & 3u;
-                    c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
+                if (coop) {
+                    c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
                 }
-            }
-            c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
-            if (lane == 0) {
-                in_bounds(g, base == lim);
-                wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
+                if (!coop || lane == 0) {
+                    in_bounds(g, base == lim);
+                    wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
+                }
             }
         }
         __syncthreads();
@@ -681,31 +703,37 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         __syncthreads();
 
         // ---- phase 6: per Q vertex b
-        for (int32_t t = warp; t < tcount; t += HUB_WARPS) {
+        // light b (short row, few P neighbours): one per thread; heavy b: one
+        // per warp
+        for (int pass = 0; pass < 2; pass++) {
+          const bool coop = pass == 1;
+          const int32_t ls = coop ? lane : 0, st = coop ? 32 : 1;
+          for (int32_t t = coop ? warp : tid; t < tcount; t += coop ? HUB_WARPS : HUB_THREADS) {
             const uint32_t b = (uint32_t)touched[t];
+            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
+            const int32_t o0 = npoff[t], o1 = npoff[t + 1];
+            if ((be - bb > 32 || o1 - o0 > 16) != coop) continue;
             uint32_t q[9];
             for (int k = 0; k < 9; k++) q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
-            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
             const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-            const int32_t o0 = npoff[t], o1 = npoff[t + 1];
             if (K == 3) {
                 // path with b at depth 2: by (colour, flag) of its P neighbours
-                if (lane < 9) {
-                    const uint32_t cls = lut[mask3((uint32_t)(lane / 3 + 1), 0u, (uint32_t)(lane % 3 + 1))];
-                    gadd(S, b, cls, q[lane], C);
+                for (int k = ls; k < 9; k += st) {
+                    const uint32_t cls = lut[mask3((uint32_t)(k / 3 + 1), 0u, (uint32_t)(k % 3 + 1))];
+                    gadd(S, b, cls, q[k], C);
                 }
                 continue;
             }
             // S4 credit of b: P neighbours x by (colour, h(x,b)), Q neighbours by flag
-            if (lane < 27) {
-                const int k = lane / 3, g3 = lane % 3;
+            for (int k27 = ls; k27 < 27; k27 += st) {
+                const int k = k27 / 3, g3 = k27 % 3;
                 const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
                 gadd(S, b, cls, (unsigned long long)q[k] * wq[(int64_t)t * 3 + g3], C);
             }
             // S2 with b adjacent to two members x, y of P, counted as if x, y
             // were not adjacent (H-adjacent pairs are corrected per H-edge):
             // pairs of NP(b) by the (colour, h(., b)) types of their members
-            for (int pr = lane; pr < 81; pr += 32) {
+            for (int pr = ls; pr < 81; pr += st) {
                 const int t1 = pr / 9, t2 = pr % 9;
                 if (t1 > t2) continue;
                 const unsigned long long cnt = t1 < t2 ? (unsigned long long)q[t1] * q[t2]
@@ -715,7 +743,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 gadd(S, b, cls, cnt, C);
                 sadd(rootD, cls, cnt);
             }
-            for (int32_t x = o0 + lane; x < o1; x += 32) {
+            for (int32_t x = o0 + ls; x < o1; x += st) {
                 const uint32_t ex = nplist[x];
                 const uint32_t xp = ex >> 2, fxb = ex & 3u;
                 const uint32_t cx = __ldg(P + xp) & 3u;
@@ -728,7 +756,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             }
             // S4 credit of each c in NQ(b); triangles v - b - c2 with c2 in
             // NQ(b), b < c2: enumerate the S3 set and correct the bulk counts
-            for (int64_t e = bu + lane; e < be; e += 32) {
+            for (int64_t e = bu + ls; e < be; e += st) {
                 const uint32_t ent = __ldg(g.col + e);
                 const uint32_t c = ent >> 2;
                 const int32_t pc = __ldcg(posmap + c);
@@ -768,6 +796,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     sadd(rootD, clB, ~0ull);
                 }
             }
+          }
         }
         __syncthreads();
 
