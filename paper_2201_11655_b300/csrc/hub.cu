@@ -657,6 +657,13 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         gadd(S, c, cls, (unsigned long long)cnt, C);
                         sadd(rootD, cls, (unsigned long long)cnt);
                     }
+                    // S2 with c adjacent to v and to another P member y: credit of
+                    // v, partners y in NP(c) by (colour, h(y,c)), counted as if v, y
+                    // were not adjacent (H-adjacent pairs are corrected per H-edge)
+                    for (int k = 0; k < 9; k++) {
+                        const uint32_t cnt = q[k] - ((uint32_t)k == (al - 1) * 3 + f - 1 ? 1u : 0u);
+                        sadd(hv, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
+                    }
                     // S2 credit of v as the P member not adjacent to c (collected in Z)
                     for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k];
                     Z[(al - 1) * 3 + f - 1] -= 1;
@@ -742,17 +749,6 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                                                (uint32_t)(t1 % 3 + 1), (uint32_t)(t2 % 3 + 1))];
                 gadd(S, b, cls, cnt, C);
                 sadd(rootD, cls, cnt);
-            }
-            for (int32_t x = o0 + ls; x < o1; x += st) {
-                const uint32_t ex = nplist[x];
-                const uint32_t xp = ex >> 2, fxb = ex & 3u;
-                const uint32_t cx = __ldg(P + xp) & 3u;
-                const int tx = (int)((cx - 1) * 3 + fxb - 1);
-                const uint32_t xv = __ldg(P + xp) >> 2;
-                for (int k = 0; k < 9; k++) {
-                    const unsigned long long cnt = q[k] - (k == tx ? 1u : 0u);
-                    gadd(S, xv, lut[mask4(cx, (uint32_t)(k / 3 + 1), 0u, 0u, fxb, (uint32_t)(k % 3 + 1))], cnt, C);
-                }
             }
             // S4 credit of each c in NQ(b); triangles v - b - c2 with c2 in
             // NQ(b), b < c2: enumerate the S3 set and correct the bulk counts
