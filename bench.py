@@ -284,7 +284,9 @@ def run_ours(args):
     wbytes = g.work_bytes(k)
     achieved = wbytes / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": load_traffic(args.workload, k), "kernel": "count_kernel<%d>" % k,
+                "traffic": load_traffic(args.workload, k),
+                "kernel": "vdmc_count: hub_kernel<%d> (root-per-CTA) overlapped with count_kernel<%d> "
+                          "(warp-per-task), timed together" % (k, k),
                 "algorithmic_bytes_per_launch": wbytes, "peak_kind": "%s hbm_gbs (copy)" % peak_kind}
 
     cpu = None

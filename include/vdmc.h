@@ -169,10 +169,12 @@ vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t
 vdmc_status vdmc_get_device_status(vdmc_graph *g);
 
 /*
- * Measurement hook: the algorithmic byte count of one vdmc_count(g, k):
- * 4 bytes per adjacency entry the method must read at least once per use --
- * N(r) for every root, N(a) for every depth-1 vertex of every root and, for
- * k = 4, N(b) for every depth-2 vertex -- plus the 8 * n * C_k bytes of the
+ * Measurement hook: the algorithmic byte count of one vdmc_count(g, k) under
+ * the current schedule: 4 bytes per adjacency entry the method must read at
+ * least once per use -- N(r) for every root, N(a) for every depth-1 vertex
+ * of every root and, for k = 4, N(b) for every depth-2 vertex (the
+ * root-per-CTA kernel reads the same rows: N(r), N(x) for x in N+(r), N(b)
+ * for the Q-neighbours b of each x) -- plus the 8 * n * C_k bytes of the
  * output and 4 * n bytes of the id map.  The cost model of the section on
  * efficacy on simulated graphs: work proportional to the neighbourhoods
  * visited.  Synchronous; runs on the legacy default stream.

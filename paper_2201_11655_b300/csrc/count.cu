@@ -255,22 +255,34 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
     }
 }
 
-// Algorithmic bytes of one count: the adjacency lists the method must read
-// at least once per use (N(r) per root, N(a) per depth-1 vertex a and, for
-// k = 4, N(b) per depth-2 vertex b), 4 bytes per entry.
-__global__ void work_bytes_kernel(Csr g, int32_t n, int k, unsigned long long *total) {
+// Algorithmic bytes of one count: the adjacency rows each method must read
+// at least once per use, 4 bytes per entry.
+//  - roots of the warp-per-task kernel (plain enumeration): N(r), N(a) for
+//    every depth-1 vertex a and, for k = 4, N(b) for every depth-2 vertex b;
+//  - roots of the root-per-CTA kernel (L >= hub_min_l): N(r), N(x) for every
+//    x in N+(r) and, for k = 4, N(b) for every Q-neighbour b of each such x
+//    (counted once per adjacency x-b).
+__global__ void work_bytes_kernel(Csr g, int32_t n, int k, int32_t hub_min_l, unsigned long long *total) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long acc = 0;
     for (int64_t r = wid; r < n; r += nw) {
         const int64_t rb = __ldg(g.rowptr + r), pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        const bool hub = hub_min_l > 0 && pe - pb >= hub_min_l;
         if (lane == 0) acc += (unsigned long long)(pe - rb);
         for (int64_t x = pb + lane; x < pe; x += 32) {
             const uint32_t a = __ldg(g.col + x) >> 2;
             const int64_t ab = __ldg(g.rowptr + a), ae = __ldg(g.rowptr + a + 1);
             acc += (unsigned long long)(ae - ab);
             if (k == 4) {
+                for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r); y < ae; y++) {
+                    const uint32_t b = __ldg(g.col + y) >> 2;
+                    if (search_row(g.col, pb, pe, b)) continue;
+                    acc += (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
+                }
+            } else if (hub) {
+                // k = 3 signature counting reads N(b) of each Q-neighbour once
                 for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r); y < ae; y++) {
                     const uint32_t b = __ldg(g.col + y) >> 2;
                     if (search_row(g.col, pb, pe, b)) continue;
@@ -409,7 +421,9 @@ extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *byt
     cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
     if (e == cudaSuccess && g->n > 0) {
         Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
-        work_bytes_kernel<<<1184, 256>>>(c, g->n, k, d);
+        vdmc_schedule_t sch;
+        vdmc_current_schedule(&sch);
+        work_bytes_kernel<<<1184, 256>>>(c, g->n, k, sch.hub_min_l, d);
         e = cudaGetLastError();
     }
     unsigned long long h = 0;
