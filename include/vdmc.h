@@ -164,6 +164,49 @@ vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank
 vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
                              void *stream);
 
+/*
+ * Allocation-free count (no counterpart in the paper; an integration aid).
+ *
+ * Some callers cannot allocate device memory at the point where they count:
+ * code that runs while a CUDA graph is being captured, real-time or serving
+ * loops that reserved a fixed device-memory budget at start-up (and where a
+ * cudaMalloc could fail, fragment the pool or stall the device), and hosts
+ * whose own allocator owns all device memory.  This entry point calls no
+ * cudaMalloc, cudaFree or allocating library routine.  It counts with the
+ * warp-per-task kernel of vdmc_count (one task per root, no root-per-CTA
+ * kernel) and keeps its scratch -- task list, work-queue cursor, status word,
+ * class tables -- in one fixed array of about 4.2 MB that every GPU holds
+ * for as long as the library is loaded.
+ *
+ * Inputs are a degree-ordered CSR in the layout vdmc_graph_export_csr
+ * returns, in device memory owned by the caller:
+ *   n          vertices, 0 <= n <= 262144 (2^18)
+ *   nnz        entries of col (2 * edges), >= 0
+ *   rowptr     int64[n+1]; col uint32[nnz] = (neighbour rank << 2) | flags,
+ *              rows sorted by neighbour rank
+ *   pbeg       int64[n]: first entry of row r whose neighbour rank is > r
+ *   new2old    int32[n]: original id of each rank
+ *   k          3 or 4
+ *   out_dev    uint64[n * C_k], overwritten, rows by original id
+ *   status_dev int32 on the device that receives the kernel's status word
+ *              (0 = ok, VDMC_ERR_DEVICE_LIMIT = an index check failed), or
+ *              NULL to use a word inside the scratch array
+ *   stream     cudaStream_t
+ * n above 2^18, k not in {3, 4}, or a NULL input returns
+ * VDMC_ERR_INVALID_ARG before any device work.
+ *
+ * The first call on a device sets the scratch up (looks up its device
+ * address and copies the class tables into it, synchronously); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one scratch array and starts by clearing its cursor and status word; calls
+ * whose work overlaps on the GPU (different streams, or concurrent host
+ * threads) race on it and must be serialised by the caller.  Asynchronous
+ * otherwise.
+ */
+vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int64_t *rowptr, const uint32_t *col,
+                                   const int64_t *pbeg, const int32_t *new2old, int k, uint64_t *out_dev,
+                                   int *status_dev, void *stream);
+
 /* After synchronising the last stream used with g: the device status word
  * (VDMC_OK or VDMC_ERR_DEVICE_LIMIT); reading it resets it to VDMC_OK. */
 vdmc_status vdmc_get_device_status(vdmc_graph *g);

@@ -449,3 +449,125 @@ extern "C" vdmc_status vdmc_get_schedule(vdmc_schedule_t *s) {
     vdmc_current_schedule(s);
     return VDMC_OK;
 }
+
+// ------------------------------------------------- allocation-free variant --
+//
+// vdmc_count_csr_noalloc: the warp-per-task count for callers that must not
+// allocate device memory.  Its scratch (task list, work-queue cursor,
+// status word, class tables) is the file-scope array below, which exists
+// once per device for as long as the library is loaded.
+
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = int64_t(1) << 18;       // vertices
+constexpr int64_t NOALLOC_MAX_TASKS = NOALLOC_MAX_N;      // one per root with L >= 1 at most
+constexpr size_t NOALLOC_HDR = 256;                        // cursor (8 B) + status (4 B), padded
+constexpr size_t NOALLOC_LUT = 4096 + 64;                  // k = 4 table, then k = 3 table
+constexpr size_t NOALLOC_BYTES = NOALLOC_HDR + NOALLOC_LUT + sizeof(Task) * (size_t)NOALLOC_MAX_TASKS;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_noalloc_scratch
+};
+NoallocDevice g_noalloc_dev[64];
+std::mutex g_noalloc_mu;
+
+// One CTA: one task per root with at least one higher-rank neighbour (the
+// whole slice of depth-1 neighbours, stride 1), in rank order; the unused
+// tail of the task array is marked empty (r = -1, skipped by the kernel).
+// Also zeroes the cursor and the status word.
+__global__ void __launch_bounds__(1024) noalloc_tasks(const int64_t *rowptr, const int64_t *pbeg, int32_t n,
+                                                      Task *tasks, int64_t max_tasks, unsigned long long *cursor,
+                                                      int *status) {
+    __shared__ int32_t warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t chunk = (n + 1023) / 1024;
+    const int32_t beg = min(n, tid * chunk), end = min(n, beg + chunk);
+    int32_t s = 0;
+    for (int32_t r = beg; r < end; r++) s += (rowptr[r + 1] - pbeg[r]) > 0;
+    int32_t inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t w = warp_tot[lane];
+        int32_t wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    int32_t o = warp_tot[warp] + inc - s;
+    for (int32_t r = beg; r < end; r++)
+        if ((rowptr[r + 1] - pbeg[r]) > 0 && o < max_tasks) tasks[o++] = Task{r, 0, 1, 0};
+    // total = exclusive prefix of the last thread + its own count
+    __syncthreads();
+    if (tid == 1023) warp_tot[0] = o;
+    __syncthreads();
+    for (int64_t t = warp_tot[0] + tid; t < max_tasks; t += 1024) tasks[t] = Task{-1, 0, 1, 0};
+    if (tid == 0) {
+        *cursor = 0ull;
+        *status = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int64_t *rowptr, const uint32_t *col,
+                                              const int64_t *pbeg, const int32_t *new2old, int k, uint64_t *out_dev,
+                                              int *status_dev, void *stream) {
+    if (k != 3 && k != 4) return VDMC_ERR_INVALID_ARG;
+    if (n < 0 || nnz < 0 || n > NOALLOC_MAX_N) return VDMC_ERR_INVALID_ARG;
+    if (n > 0 && (!rowptr || !pbeg || !new2old || !out_dev || (nnz > 0 && !col))) return VDMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    VDMC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return VDMC_ERR_INVALID_ARG;
+    unsigned char *base = nullptr;
+    {
+        // once per device: the device address of the scratch array and the
+        // class tables copied into it (plain copies, no allocation)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        NoallocDevice &D = g_noalloc_dev[dev];
+        if (!D.ready) {
+            void *p = nullptr;
+            VDMC_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            unsigned char *b = (unsigned char *)p;
+            VDMC_CUDA_TRY(cudaMemcpy(b + NOALLOC_HDR, vdmc_host_lut(4), 4096, cudaMemcpyHostToDevice));
+            VDMC_CUDA_TRY(cudaMemcpy(b + NOALLOC_HDR + 4096, vdmc_host_lut(3), 64, cudaMemcpyHostToDevice));
+            D.base = b;
+            D.ready = true;
+        }
+        base = D.base;
+    }
+    const int C = k == 3 ? 13 : 199;
+    unsigned long long *cursor = (unsigned long long *)base;
+    int *status = status_dev ? status_dev : (int *)(base + 8);
+    const uint8_t *lut = base + NOALLOC_HDR + (k == 4 ? 0 : 4096);
+    Task *tasks = (Task *)(base + NOALLOC_HDR + NOALLOC_LUT);
+    if (n == 0) return VDMC_OK;
+    VDMC_CUDA_TRY(cudaMemsetAsync(out_dev, 0, sizeof(uint64_t) * (size_t)n * C, s));
+    noalloc_tasks<<<1, 1024, 0, s>>>(rowptr, pbeg, n, tasks, NOALLOC_MAX_TASKS, cursor, status);
+    VDMC_CUDA_TRY(cudaGetLastError());
+    vdmc_schedule_t sch;
+    vdmc_current_schedule(&sch);
+    const int warps = std::max(1, std::min(8, sch.warps_per_block));
+    const size_t smem = smem_bytes(k, warps);
+    int sms = 0, per_sm = 0;
+    VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kern = (k == 3) ? count_kernel<3> : count_kernel<4>;
+    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
+    const int64_t grid = (int64_t)sms * std::max(1, per_sm);
+    GraphDesc d{rowptr, col, pbeg, new2old, out_dev, n, 0, nnz};
+    kern<<<(unsigned)grid, warps * 32, smem, s>>>(d, nullptr, tasks, NOALLOC_MAX_TASKS, cursor, lut, 0, n, status);
+    VDMC_CUDA_TRY(cudaGetLastError());
+    return VDMC_OK;
+}
