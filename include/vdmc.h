@@ -63,6 +63,7 @@ typedef struct {
     int64_t reciprocal_pairs;  /* edges of G_U carrying arcs both ways */
     int64_t num_tasks;         /* (root, depth-1 slice) work items of the warp kernel */
     int64_t num_hub_roots;     /* roots handled by the root-per-CTA kernel */
+    int64_t num_graphs;        /* graphs in the union (vdmc_graph_create_batch), else 1 */
     int64_t device_bytes;      /* bytes held on the device by this graph */
 } vdmc_graph_info_t;
 
@@ -99,6 +100,26 @@ typedef struct {
  */
 vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                               int ptrs_on_device, void *stream, vdmc_graph **out);
+
+/*
+ * Build ONE graph from many independent graphs (a batch; no paper
+ * counterpart): the disjoint union of graphs 0..num-1.
+ *   num        number of graphs, >= 1
+ *   ns, ms     host int32[num] vertex counts and int64[num] arc counts
+ *   src, dst   the graphs' arc lists concatenated in graph order (arcs of
+ *              graph i first, then graph i+1, ...), each in that graph's
+ *              LOCAL ids 0..ns[i]-1; host or device pointers as for
+ *              vdmc_graph_create
+ * Vertex x of graph i becomes vertex voff[i] + x of the union, with
+ * voff[i] = ns[0] + ... + ns[i-1]; the union's total vertex count must be
+ * < 2^30.  No k-set of the union spans two graphs (they are not connected),
+ * so one vdmc_count on the union counts all graphs in one launch and graph
+ * i's counts are rows voff[i] .. voff[i+1]-1 of the output.  A local id
+ * outside [0, ns[i]) returns VDMC_ERR_OUT_OF_RANGE_VERTEX.  Synchronises
+ * `stream`.
+ */
+vdmc_status vdmc_graph_create_batch(int32_t num, const int32_t *ns, const int64_t *ms, const int32_t *src,
+                                    const int32_t *dst, int ptrs_on_device, void *stream, vdmc_graph **out);
 
 /* Free the graph's device memory (synchronises the device first). */
 vdmc_status vdmc_graph_destroy(vdmc_graph *g);
@@ -154,12 +175,17 @@ vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank
                              uint64_t *out_dev, void *stream);
 
 /*
- * Count `num` independent graphs in ONE persistent launch (a batch of
- * uneven small graphs; no paper counterpart).  outs[i] is a device
+ * Count `num` independent graphs, built one by one, in ONE launch (a batch
+ * of uneven small graphs; no paper counterpart).  outs[i] is a device
  * uint64[n_i * C_k] for graphs[i], overwritten.  `graphs` and `outs` are
  * host arrays.  Results equal num separate vdmc_count calls bit for bit.
- * The graphs must not be used by another call until the stream reaches this
- * point.
+ * The first call for a given (graphs, outs, k, schedule) concatenates the
+ * graphs' CSRs into a plan cached on graphs[0] (allocates; synchronises
+ * `stream`), counts and scatters the rows to outs; the second call captures
+ * the count and scatter into a CUDA graph and later calls replay it.  Any
+ * change of graphs, outs, k or schedule rebuilds the plan.  Plans die with
+ * graphs[0]; destroying another member graph makes the plan stale, so build
+ * a new list after destroying graphs.  Calls on one plan must not overlap.
  */
 vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
                              void *stream);

@@ -50,7 +50,9 @@ struct DevLut {
 DevLut g_lut[64];  // per device
 std::mutex g_lut_mu;
 
-cudaError_t device_lut(int k, const uint8_t **out) {
+}  // namespace
+
+cudaError_t vdmc_device_lut(int k, const uint8_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -71,6 +73,9 @@ cudaError_t device_lut(int k, const uint8_t **out) {
     *out = g_lut[dev].lut[k];
     return cudaSuccess;
 }
+
+namespace {
+cudaError_t device_lut(int k, const uint8_t **out) { return vdmc_device_lut(k, out); }
 
 // ------------------------------------------------------------ tasks -----
 
@@ -365,7 +370,7 @@ vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, 
     return vdmc_build_hubs(g, hub_min_l, s);
 }
 
-static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s) {
+vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s) {
     if (!g || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
     if (!out && g->n > 0) return VDMC_ERR_INVALID_ARG;
     const int C = k == 3 ? 13 : 199;
@@ -394,24 +399,13 @@ static vdmc_status count_impl(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint
 }
 
 extern "C" vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {
-    return count_impl(g, k, 0, g ? g->n : 0, out_dev, (cudaStream_t)stream);
+    return vdmc_count_internal(g, k, 0, g ? g->n : 0, out_dev, (cudaStream_t)stream);
 }
 
 extern "C" vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank_hi, uint64_t *out_dev,
                                         void *stream) {
     if (!g || rank_lo < 0 || rank_hi < rank_lo) return VDMC_ERR_INVALID_ARG;
-    return count_impl(g, k, rank_lo, std::min(rank_hi, g->n), out_dev, (cudaStream_t)stream);
-}
-
-extern "C" vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
-                                        void *stream) {
-    // First version: one launch per graph on the same stream.
-    if (num < 0 || (num > 0 && (!graphs || !outs))) return VDMC_ERR_INVALID_ARG;
-    for (int i = 0; i < num; i++) {
-        vdmc_status st = vdmc_count(graphs[i], k, outs[i], stream);
-        if (st != VDMC_OK) return st;
-    }
-    return VDMC_OK;
+    return vdmc_count_internal(g, k, rank_lo, std::min(rank_hi, g->n), out_dev, (cudaStream_t)stream);
 }
 
 extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes) {

@@ -198,6 +198,7 @@ void free_graph_buffers(vdmc_graph *g) {
     cudaFree(g->qhead);
     cudaFree(g->status);
     vdmc_hub_free(g);
+    vdmc_batch_plan_free(g);
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
@@ -211,9 +212,12 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     VDMC_CUDA_TRY(cudaGetDevice(&g->device));
     VDMC_CUDA_TRY(cudaMalloc((void **)&g->qhead, sizeof(unsigned long long)));
     VDMC_CUDA_TRY(cudaMalloc((void **)&g->status, sizeof(int)));
-    VDMC_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
-    VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
-    VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    {
+        vdmc_status st0 = vdmc_graph_init_streams(g);
+        if (st0 != VDMC_OK) return st0;
+    }
+    g->serial = vdmc_next_serial();
+    g->num_graphs = 1;
     VDMC_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), s));
 
     Tmp tmp(s);
@@ -394,6 +398,7 @@ extern "C" vdmc_status vdmc_graph_destroy(vdmc_graph *g) {
 extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *info) {
     if (!g || !info) return VDMC_ERR_INVALID_ARG;
     *info = g->info;
+    info->num_graphs = g->num_graphs;
     info->num_tasks = g->ntasks;
     info->num_hub_roots = g->nhubs;
     info->device_bytes += (int64_t)g->hub_scratch_bytes;

@@ -58,6 +58,9 @@ struct vdmc_graph {
     unsigned long long *hub_qhead;
     cudaStream_t side;           // second stream: the two kernels overlap
     cudaEvent_t ev_fork, ev_join;
+    uint64_t serial;             // creation number (identifies the graph in cached batch plans)
+    int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
+    void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
 };
 
 // ---- status helpers ----
@@ -87,6 +90,15 @@ cudaError_t vdmc_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t count, in
 // induced graph is not weakly connected.  Built once per k, host memory.
 const uint8_t *vdmc_host_lut(int k);
 const uint16_t *vdmc_host_canon(int k, int *num_classes);
+
+// ---- counting (count.cu) ----
+vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s);
+cudaError_t vdmc_device_lut(int k, const uint8_t **out);
+
+// ---- batch plans (batch.cu) ----
+void vdmc_batch_plan_free(vdmc_graph *g);
+uint64_t vdmc_next_serial();
+vdmc_status vdmc_graph_init_streams(vdmc_graph *g);
 
 // ---- schedule / tasks (count.cu) ----
 vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, cudaStream_t s);

@@ -34,7 +34,7 @@ class GraphInfo(ctypes.Structure):
         ("n", ctypes.c_int32), ("max_degree", ctypes.c_int32), ("arcs_in", ctypes.c_int64),
         ("self_loops", ctypes.c_int64), ("duplicate_arcs", ctypes.c_int64), ("arcs_kept", ctypes.c_int64),
         ("edges_u", ctypes.c_int64), ("reciprocal_pairs", ctypes.c_int64), ("num_tasks", ctypes.c_int64),
-        ("num_hub_roots", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("num_hub_roots", ctypes.c_int64), ("num_graphs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -62,6 +62,9 @@ def _lib():
         sig = {
             "vdmc_graph_create": ([i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
             "vdmc_graph_destroy": ([vp], ctypes.c_int),
+            "vdmc_graph_create_batch": ([ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)],
+                                        ctypes.c_int),
+            "vdmc_count_csr_noalloc": ([i32, i64, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
             "vdmc_graph_info": ([vp, ctypes.POINTER(GraphInfo)], ctypes.c_int),
             "vdmc_graph_export_csr": ([vp, vp, vp, vp], ctypes.c_int),
             "vdmc_num_classes": ([ctypes.c_int], ctypes.c_int),
@@ -204,6 +207,27 @@ def graph_create(n: int, src, dst, stream=None) -> Graph:
     return Graph(h, int(n))
 
 
+def graph_create_batch(graphs, stream=None) -> Graph:
+    """Build the disjoint union of many graphs [(n, src, dst), ...] (local ids) as one device graph.
+
+    Graph i's counts are rows offsets[i] .. offsets[i+1]-1 of a count on the
+    returned graph; ``Graph.offsets`` holds those offsets."""
+    lib = _lib()
+    num = len(graphs)
+    ns = np.array([int(g[0]) for g in graphs], dtype=np.int32)
+    ms = np.array([len(g[1]) for g in graphs], dtype=np.int64)
+    src = np.ascontiguousarray(np.concatenate([np.asarray(g[1], np.int32) for g in graphs]) if num else
+                               np.zeros(0, np.int32))
+    dst = np.ascontiguousarray(np.concatenate([np.asarray(g[2], np.int32) for g in graphs]) if num else
+                               np.zeros(0, np.int32))
+    h = ctypes.c_void_p()
+    _check(lib.vdmc_graph_create_batch(num, ns.ctypes.data, ms.ctypes.data, src.ctypes.data, dst.ctypes.data, 0,
+                                       _stream_ptr(stream), ctypes.byref(h)), "vdmc_graph_create_batch")
+    g = Graph(h, int(ns.sum()))
+    g.offsets = np.concatenate([[0], np.cumsum(ns.astype(np.int64))])
+    return g
+
+
 def _out_tensor(g: Graph, k: int, out):
     import torch
     nc = num_classes(k)
@@ -235,7 +259,7 @@ def count_batch(graphs, k: int, outs=None, stream=None):
     """Count many graphs in one launch; returns the list of output tensors."""
     outs = [_out_tensor(g, k, None if outs is None else outs[i]) for i, g in enumerate(graphs)]
     num = len(graphs)
-    harr = (ctypes.c_void_p * max(num, 1))(*[g.handle for g in graphs])
+    harr = (ctypes.c_void_p * max(num, 1))(*[g.handle.value for g in graphs])
     oarr = (ctypes.c_void_p * max(num, 1))(*[o.data_ptr() for o in outs])
     _check(_lib().vdmc_count_batch(harr, num, int(k), oarr, _stream_ptr(stream)), "vdmc_count_batch")
     return outs

@@ -1,0 +1,110 @@
+"""Batched counting: many uneven graphs in one launch, bit-exact.
+
+Two routes: the concatenated union built from arc lists
+(vdmc_graph_create_batch + one vdmc_count), and vdmc_count_batch over
+separately built graphs (cached plan, then a captured CUDA graph replayed).
+Both must equal one plain count per graph -- and the oracle -- exactly.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_util import gpu_count, to_numpy_u64
+from oracle import oracle as O
+from paper_2201_11655_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_11655_b300 import build, vdmc
+    build.build()
+    vdmc.load()
+
+
+def small_batch(num, seed, n_hi=120):
+    return synth.batch(num, seed, n_lo=10, n_hi=n_hi)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_union_matches_oracle_per_graph(k):
+    from paper_2201_11655_b300 import vdmc
+    graphs = small_batch(120, 5)
+    with vdmc.graph_create_batch(graphs) as U:
+        assert U.info()["num_graphs"] == len(graphs)
+        out = to_numpy_u64(vdmc.count(U, k))
+        torch.cuda.synchronize()
+        assert U.device_status() == 0
+    off = U.offsets
+    for i, (n, s, d) in enumerate(graphs):
+        want, _ = O.count(n, s, d, k)
+        np.testing.assert_array_equal(out[off[i]:off[i + 1]], want, err_msg="graph %d" % i)
+
+
+def test_union_with_hub_kernel_matches_plain_per_graph():
+    from paper_2201_11655_b300 import vdmc
+    graphs = small_batch(300, 9, n_hi=500)
+    old = vdmc.get_schedule()
+    try:
+        vdmc.set_schedule(hub_min_l=16)
+        with vdmc.graph_create_batch(graphs) as U:
+            assert U.info()["num_hub_roots"] > 0
+            out = to_numpy_u64(vdmc.count(U, 4))
+        vdmc.set_schedule(hub_min_l=0)
+        for i in range(0, len(graphs), 7):
+            n, s, d = graphs[i]
+            np.testing.assert_array_equal(out[U.offsets[i]:U.offsets[i + 1]], gpu_count(n, s, d, 4))
+    finally:
+        vdmc.set_schedule(**old)
+
+
+def test_count_batch_plan_capture_replay():
+    from paper_2201_11655_b300 import vdmc
+    graphs = small_batch(80, 13, n_hi=300)
+    gs = [vdmc.graph_create(n, s, d) for n, s, d in graphs]
+    try:
+        for k in (3, 4):
+            want = [to_numpy_u64(vdmc.count(g, k)) for g in gs]
+            outs = [torch.full((g.n, vdmc.num_classes(k)), 9, dtype=torch.int64, device="cuda").view(torch.uint64)
+                    for g in gs]
+            for call in range(4):  # direct, capture, replay, replay
+                for o in outs:
+                    o.view(torch.int64).fill_(3)
+                vdmc.count_batch(gs, k, outs=outs)
+                torch.cuda.synchronize()
+                for i in range(len(gs)):
+                    np.testing.assert_array_equal(to_numpy_u64(outs[i]), want[i], err_msg="k=%d call %d g %d" % (k, call, i))
+            # new output buffers: the plan is rebuilt, results unchanged
+            outs2 = vdmc.count_batch(gs, k)
+            torch.cuda.synchronize()
+            for i in range(len(gs)):
+                np.testing.assert_array_equal(to_numpy_u64(outs2[i]), want[i])
+    finally:
+        for g in gs:
+            g.close()
+
+
+def test_batch_degenerate_members():
+    from paper_2201_11655_b300 import vdmc
+    e = np.zeros(0, np.int32)
+    graphs = [(5, e, e), (0, e, e), (3, np.array([0, 1], np.int32), np.array([1, 2], np.int32)),
+              synth.gnp(30, 0.2, 1)]
+    with vdmc.graph_create_batch(graphs) as U:
+        out = to_numpy_u64(vdmc.count(U, 3))
+    for i, (n, s, d) in enumerate(graphs):
+        want, _ = O.count(n, s, d, 3)
+        np.testing.assert_array_equal(out[U.offsets[i]:U.offsets[i + 1]], want)
+
+
+def test_batch_rejects_local_id_out_of_range():
+    from paper_2201_11655_b300 import vdmc
+    graphs = [(4, np.array([0, 1], np.int32), np.array([1, 2], np.int32)),
+              (3, np.array([0, 3], np.int32), np.array([1, 1], np.int32))]  # 3 is not a vertex of graph 1
+    with pytest.raises(vdmc.VdmcError) as ei:
+        vdmc.graph_create_batch(graphs)
+    assert ei.value.status == 2
