@@ -109,6 +109,7 @@ struct Plan {
     uint64_t **outs_d = nullptr;    // num
     int num = 0;
     int calls = 0;
+    cudaStream_t cap = nullptr;     // private stream the count is captured on
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -132,6 +133,7 @@ void plan_free(Plan *p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
     free_union(&p->U);
     cudaFree(p->uout);
     cudaFree(p->roff_d);
@@ -259,11 +261,15 @@ extern "C" vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int 
     p->calls++;
     if (p->calls == 1) return run_plan(p, s);  // direct; allocates the count's lazily created scratch
     if (!p->exec) {
-        // capture the count + scatter once, replay it from now on
-        VDMC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-        vdmc_status st = run_plan(p, s);
+        // capture the count + scatter once on the plan's own stream (the
+        // caller's stream may be the legacy default stream, which cannot be
+        // captured); every later call replays it on the caller's stream
+        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!p->cap) VDMC_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+        VDMC_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed));
+        vdmc_status st = run_plan(p, p->cap);
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
         if (st != VDMC_OK) {
             if (graph) cudaGraphDestroy(graph);
             return st;
