@@ -49,6 +49,15 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle sample time")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--batch-graphs", type=int, default=50_000)
+    p.add_argument("--batch-compare", type=int, default=2_000,
+                   help="graphs of the batch also counted one launch per graph")
+    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-n-hi", type=int, default=50_000)
+    p.add_argument("--serve-rate", type=float, default=400.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--no-tuned", action="store_true", help="keep the library's default schedule")
     return p.parse_args()
 
 
@@ -165,6 +174,97 @@ def oracle_sample(n, s, d, k, target_s, threads=None):
                       "subtracted)" % (threads, lo, hi, found, k, el, build_s), "lo": lo, "hi": hi}
 
 
+def bench_batch(args, k):
+    """Batched graphs/s: many small uneven graphs (n log-uniform in [10, 500],
+    half G(n,p), half Chung-Lu, p ~ U[0.02, 0.2]) counted in one launch over
+    their concatenated CSR, against one vdmc_count launch per graph on a
+    subset (same pre-built graphs; builds excluded from both), and against
+    vdmc_count_batch (cached plan, CUDA-graph replay) on that subset."""
+    import numpy as np
+    import torch
+    from paper_2201_11655_b300 import synth, vdmc
+    C = vdmc.num_classes(k)
+    t0 = time.perf_counter()
+    graphs = synth.batch(args.batch_graphs, 4)
+    gen_s = time.perf_counter() - t0
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b2.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b2))
+        return best
+
+    t0 = time.perf_counter()
+    U = vdmc.graph_create_batch(graphs)
+    build_s = time.perf_counter() - t0
+    out = torch.empty((U.n, C), dtype=torch.uint64, device="cuda")
+    ms_union = timed(lambda: vdmc.count(U, k, out))
+    inst = int(out.view(torch.int64).sum().item()) // k
+    U.close()
+    sub = graphs[:args.batch_compare]
+    gs = [vdmc.graph_create(n, s, d) for n, s, d in sub]
+    outs = [torch.empty((g.n, C), dtype=torch.uint64, device="cuda") for g in gs]
+    ms_each = timed(lambda: [vdmc.count(g, k, o) for g, o in zip(gs, outs)], reps=1)
+    ms_plan = timed(lambda: vdmc.count_batch(gs, k, outs=outs))
+    Us = vdmc.graph_create_batch(sub)
+    outs_u = torch.empty((Us.n, C), dtype=torch.uint64, device="cuda")
+    ms_union_sub = timed(lambda: vdmc.count(Us, k, outs_u))
+    # identical results: union rows == per-graph counts
+    vdmc.count(Us, k, outs_u)
+    [vdmc.count(g, k, o) for g, o in zip(gs, outs)]
+    torch.cuda.synchronize()
+    same = all(torch.equal(outs_u[Us.offsets[i]:Us.offsets[i + 1]].view(torch.int64), outs[i].view(torch.int64))
+               for i in range(len(gs)))
+    Us.close()
+    for g in gs:
+        g.close()
+    return {"workload": "%d graphs, n log-uniform [10,500], G(n,p) / Chung-Lu 2.5, p~U[0.02,0.2]" % len(graphs),
+            "k": k, "graphs_per_s": len(graphs) / (ms_union / 1e3), "ms_per_batch": ms_union,
+            "instances_per_s": inst / (ms_union / 1e3), "instances": inst, "union_build_s": build_s,
+            "generate_s": gen_s,
+            "subset": {"graphs": len(sub), "one_launch_per_graph_graphs_per_s": len(sub) / (ms_each / 1e3),
+                       "count_batch_replay_graphs_per_s": len(sub) / (ms_plan / 1e3),
+                       "union_graphs_per_s": len(sub) / (ms_union_sub / 1e3), "identical_results": bool(same)}}
+
+
+def bench_serve(args):
+    """Served requests: Poisson arrivals of count requests over directed
+    Chung-Lu graphs (n log-uniform in [10^3, 5*10^4] by default -- the full
+    [10^3, 2*10^6] stream is a long run, see --serve-n-hi/--serve-requests --
+    mean out-degree U[4,16], exponent U[2.1,2.8], k in {3,4} 50/50) through
+    the continuous-batching loop; throughput and latency."""
+    import torch
+    from paper_2201_11655_b300 import synth
+    from paper_2201_11655_b300.serve import GpuBackend, Request, Server
+    specs = synth.serve_requests(args.serve_requests, 5, rate_hz=args.serve_rate, n_lo=1000, n_hi=args.serve_n_hi)
+    reqs = []
+    for i, sp in enumerate(specs):
+        n, s, d = synth.chung_lu(sp["n"], sp["mean_out_degree"], sp["exponent"], sp["seed"])
+        reqs.append(Request(rid=i, n=n, src=s, dst=d, k=sp["k"], arrival=sp["t"]))
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.5)
+    srv = Server(GpuBackend(), memory_budget=budget, max_inflight=6, small_n=20_000, batch_max=64,
+                 batch_wait=0.002)
+    t0 = time.perf_counter()
+    srv.submit_stream(reqs)
+    done = srv.run()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = Server.latency_stats(done)
+    return {"requests": len(reqs), "rate_hz": args.serve_rate, "n_range": [1000, args.serve_n_hi],
+            "requests_per_s": len(done) / wall, "wall_s": wall, "latency": st,
+            "errors": sum(1 for r in done if r.error), "memory_budget_bytes": budget,
+            "peak_reserved_bytes": srv.peak_reserved,
+            "batches": len({r.job for r in done}), "max_inflight": srv.max_inflight}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -217,6 +317,10 @@ def run_ours(args):
     C = vdmc.num_classes(k)
     n, s, d = synth.workload(args.workload)
     m = int(s.size)
+    tuned = None
+    if not args.no_tuned:
+        from paper_2201_11655_b300 import autotune
+        tuned = autotune.apply_tuned(k, n, m)
     stream = torch.cuda.current_stream()
     src_dev = torch.from_numpy(s).cuda()
     dst_dev = torch.from_numpy(d).cuda()
@@ -299,6 +403,11 @@ def run_ours(args):
             cpu = {"value": None, "unit": "instances/s", "cores": None, "kind": "oracle", "sample": "failed: %s" % ex}
 
     g.close()
+    batch = serve = None
+    if rank == 0 and not args.no_batch:
+        batch = bench_batch(args, k)
+    if rank == 0 and not args.no_serve:
+        serve = bench_serve(args)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC % k, "value": value, "unit": "instances/s", "n_gpus": world, "steps": args.steps,
@@ -310,7 +419,8 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single",
                        "schedule": vdmc.get_schedule()},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "step_ms": step_ms,
+            "cpu_baseline": cpu, "step_ms": step_ms, "batch": batch, "serve": serve,
+            "schedule_source": "tuned" if tuned else "default",
         }), flush=True)
     if dist:
         dist.destroy_process_group()

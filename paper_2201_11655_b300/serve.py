@@ -1,0 +1,281 @@
+"""Serving loop: continuous batching of count requests on one GPU.
+
+Requests (a directed graph and k) arrive over time.  The loop
+  * admits a request only while the estimated device memory of everything in
+    flight stays within a budget, so large graphs wait for memory to free up;
+  * coalesces small requests of the same k into one union graph
+    (``vdmc_graph_create_batch``) counted by one launch, and runs each large
+    request on a stream of its own, so their work overlaps on the device;
+  * keeps each result's uint64 counters resident on the device (a view of
+    its job's output) and records arrival, admission and completion times.
+
+Counting is done by the CUDA library; this module only schedules.  The
+scheduling logic talks to a *backend* (``GpuBackend`` here; the tests also use
+a simulated one), so it can be exercised without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, List, Optional
+
+import numpy as np
+
+C_K = {3: 13, 4: 199}
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    n: int
+    src: np.ndarray
+    dst: np.ndarray
+    k: int
+    arrival: float = 0.0            # seconds on the server clock
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    counts: object = None           # device uint64 tensor [n, C_k] once done
+    error: Optional[str] = None
+    job: Optional[int] = None       # id of the job that counted it
+
+    @property
+    def m(self) -> int:
+        return int(len(self.src))
+
+    @property
+    def latency(self) -> Optional[float]:
+        return None if self.done is None else self.done - self.arrival
+
+
+def footprint_bytes(n: int, m: int, k: int, hub_slots: int = 148) -> int:
+    """Upper estimate of the device memory one count of (n, m, k) holds at peak.
+
+    Build temporaries (~72 bytes per arc), the CSR and id maps (~48 bytes per
+    vertex plus 8 per arc), the output (8 * C_k per vertex) and the scratch of
+    the root-per-CTA kernel (per slot: a position map of 4 bytes per vertex
+    and ~60 bytes per distinct second-hop vertex, at most min(n, 2m))."""
+    slots = max(1, min(hub_slots, n // 64))
+    hub = slots * (4 * n + 60 * min(n, 2 * m)) if n >= 64 else 0
+    return int(80 * m + 48 * n + 8 * C_K[k] * n + hub + (1 << 20))
+
+
+class Job:
+    def __init__(self, jid, reqs, kind):
+        self.jid = jid
+        self.reqs = reqs
+        self.kind = kind          # "single" or "batch"
+        self.reserved = 0
+        self.handle = None
+        self.launched = None
+
+
+class Server:
+    """Continuous-batching request loop (single device).
+
+    memory_budget   bytes the in-flight jobs may hold together
+    max_inflight    jobs on the device at once (one stream each)
+    small_n         requests with n <= small_n are batched
+    batch_max       most requests per batch
+    batch_wait      seconds a small request may wait for companions while
+                    the device is busy
+    """
+
+    def __init__(self, backend, memory_budget: int, max_inflight: int = 4, small_n: int = 20_000,
+                 batch_max: int = 256, batch_wait: float = 0.002, clock: Callable[[], float] = time.perf_counter):
+        self.backend = backend
+        self.budget = int(memory_budget)
+        self.max_inflight = max_inflight
+        self.small_n = small_n
+        self.batch_max = batch_max
+        self.batch_wait = batch_wait
+        self.clock = clock
+        self.t0 = clock()
+        self.arrivals = collections.deque()      # not yet arrived (sorted by arrival)
+        self.small = {3: collections.deque(), 4: collections.deque()}
+        self.large = collections.deque()
+        self.inflight: List[Job] = []
+        self.reserved = 0
+        self.peak_reserved = 0
+        self.completed: List[Request] = []
+        self._jid = 0
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    # -- intake ---------------------------------------------------------
+    def submit(self, req: Request, at: Optional[float] = None):
+        """Queue a request; ``at`` (server clock) defaults to now."""
+        req.arrival = self.now() if at is None else at
+        self.arrivals.append(req)
+
+    def submit_stream(self, reqs: List[Request]):
+        """Queue a timed stream (arrival offsets relative to now)."""
+        base = self.now()
+        for r in sorted(reqs, key=lambda r: r.arrival):
+            r.arrival = base + r.arrival
+            self.arrivals.append(r)
+
+    # -- scheduling -----------------------------------------------------
+    def _estimate(self, reqs) -> int:
+        if len(reqs) == 1:
+            r = reqs[0]
+            return footprint_bytes(r.n, r.m, r.k)
+        n = sum(r.n for r in reqs)
+        m = sum(r.m for r in reqs)
+        return footprint_bytes(n, m, reqs[0].k)
+
+    def _fits(self, need: int) -> bool:
+        # a job larger than the whole budget may run alone
+        return self.reserved + need <= self.budget or (not self.inflight and self.reserved == 0)
+
+    def _launch(self, reqs, kind, now):
+        need = self._estimate(reqs)
+        self._jid += 1
+        job = Job(self._jid, reqs, kind)
+        job.reserved = need
+        job.launched = now
+        for r in reqs:
+            r.admitted = now
+            r.job = job.jid
+        try:
+            job.handle = self.backend.launch(reqs)
+        except Exception as ex:  # a failed request does not stop the loop
+            for r in reqs:
+                r.error = str(ex)
+                r.done = self.now()
+                self.completed.append(r)
+            return
+        self.reserved += need
+        self.peak_reserved = max(self.peak_reserved, self.reserved)
+        self.inflight.append(job)
+
+    def poll(self) -> List[Request]:
+        """One scheduling pass; returns the requests completed in it."""
+        done_now = []
+        # 1. completions free memory and streams
+        still = []
+        for job in self.inflight:
+            if self.backend.done(job.handle):
+                results = self.backend.finish(job.handle)
+                t = self.now()
+                for r, res in zip(job.reqs, results):
+                    r.counts = res
+                    r.done = t
+                    done_now.append(r)
+                self.reserved -= job.reserved
+            else:
+                still.append(job)
+        self.inflight = still
+        # 2. arrivals
+        now = self.now()
+        while self.arrivals and self.arrivals[0].arrival <= now:
+            r = self.arrivals.popleft()
+            (self.small[r.k] if r.n <= self.small_n else self.large).append(r)
+        # 3. large requests, FIFO, while memory and streams allow
+        while self.large and len(self.inflight) < self.max_inflight:
+            r = self.large[0]
+            if not self._fits(self._estimate([r])):
+                break
+            self.large.popleft()
+            self._launch([r], "single", now)
+        # 4. small requests coalesced per k
+        for k in (3, 4):
+            q = self.small[k]
+            while q and len(self.inflight) < self.max_inflight:
+                waited = now - q[0].arrival
+                if len(q) < self.batch_max and self.inflight and waited < self.batch_wait:
+                    break
+                group = []
+                while q and len(group) < self.batch_max:
+                    cand = group + [q[0]]
+                    if group and not self._fits(self._estimate(cand)):
+                        break
+                    group.append(q.popleft())
+                if not self._fits(self._estimate(group)):
+                    for r in reversed(group):
+                        q.appendleft(r)
+                    break
+                self._launch(group, "batch" if len(group) > 1 else "single", now)
+        self.completed.extend(done_now)
+        return done_now
+
+    def idle(self) -> bool:
+        return not (self.arrivals or self.large or self.small[3] or self.small[4] or self.inflight)
+
+    def run(self, sleep: float = 0.0002, timeout: float = 3600.0) -> List[Request]:
+        """Serve until every submitted request is done; returns them in completion order."""
+        t_end = self.now() + timeout
+        while not self.idle():
+            if not self.poll():
+                if self.now() > t_end:
+                    raise TimeoutError("serving loop did not drain")
+                if sleep:
+                    time.sleep(sleep)
+        return self.completed
+
+    @staticmethod
+    def latency_stats(reqs: List[Request]) -> dict:
+        lat = np.array([r.latency for r in reqs if r.latency is not None and r.error is None])
+        if lat.size == 0:
+            return {"count": 0}
+        return {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "max_ms": float(lat.max() * 1e3)}
+
+
+class GpuBackend:
+    """Runs jobs with the CUDA library: one torch stream per in-flight job."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        from . import vdmc
+        self.torch = torch
+        self.vdmc = vdmc
+        self.device = device
+        vdmc.load()
+        self.free_streams = []
+
+    def _stream(self):
+        return self.free_streams.pop() if self.free_streams else self.torch.cuda.Stream(device=self.device)
+
+    def launch(self, reqs):
+        torch, vdmc = self.torch, self.vdmc
+        k = reqs[0].k
+        stream = self._stream()
+        with torch.cuda.stream(stream):
+            if len(reqs) == 1:
+                r = reqs[0]
+                g = vdmc.graph_create(r.n, r.src, r.dst, stream=stream)
+                offsets = [0, r.n]
+            else:
+                g = vdmc.graph_create_batch([(r.n, r.src, r.dst) for r in reqs], stream=stream)
+                offsets = g.offsets
+            out = torch.empty((g.n, vdmc.num_classes(k)), dtype=torch.uint64, device="cuda")
+            vdmc.count(g, k, out=out, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return {"g": g, "out": out, "ev": ev, "stream": stream, "offsets": offsets, "n": len(reqs)}
+
+    def done(self, h) -> bool:
+        return h["ev"].query()
+
+    def finish(self, h):
+        g = h["g"]
+        st = g.device_status()
+        g.close()
+        self.free_streams.append(h["stream"])
+        if st != 0:
+            raise RuntimeError("device status %d" % st)
+        off = h["offsets"]
+        return [h["out"][int(off[i]):int(off[i + 1])] for i in range(h["n"])]
+
+
+def requests_from_stream(specs, draw) -> List[Request]:
+    """Requests from ``synth.serve_requests`` specs; ``draw(spec)`` returns (n, src, dst)."""
+    out = []
+    for i, sp in enumerate(specs):
+        n, s, d = draw(sp)
+        out.append(Request(rid=i, n=n, src=s, dst=d, k=sp["k"], arrival=sp["t"]))
+    return out
