@@ -201,6 +201,10 @@ def bench_batch(args, k):
             best = min(best, a.elapsed_time(b2))
         return best
 
+    from paper_2201_11655_b300 import autotune
+    saved = vdmc.get_schedule()
+    tuned = None if args.no_tuned else autotune.apply_tuned(k, sum(g[0] for g in graphs),
+                                                            sum(len(g[1]) for g in graphs))
     t0 = time.perf_counter()
     U = vdmc.graph_create_batch(graphs)
     build_s = time.perf_counter() - t0
@@ -225,7 +229,9 @@ def bench_batch(args, k):
     Us.close()
     for g in gs:
         g.close()
+    vdmc.set_schedule(**saved)
     return {"workload": "%d graphs, n log-uniform [10,500], G(n,p) / Chung-Lu 2.5, p~U[0.02,0.2]" % len(graphs),
+            "schedule": tuned or saved, "schedule_source": "tuned" if tuned else "default",
             "k": k, "graphs_per_s": len(graphs) / (ms_union / 1e3), "ms_per_batch": ms_union,
             "instances_per_s": inst / (ms_union / 1e3), "instances": inst, "union_build_s": build_s,
             "generate_s": gen_s,

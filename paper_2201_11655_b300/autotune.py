@@ -32,7 +32,8 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNED_PATH = os.path.join(HERE, "tuned_schedules.json")
 
-STAGE1 = [{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (16, 32, 64, 128, 256) for b in (1, 2)]
+STAGE1 = ([{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (16, 32, 64, 128, 256, 1024) for b in (1, 2)] +
+          [{"hub_min_l": 0, "hub_blocks_per_sm": 1}])
 STAGE2 = [{"a_chunk": a, "warps_per_block": w} for a in (4, 16, 64) for w in (4, 8)]
 
 
