@@ -123,6 +123,7 @@ void free_union(vdmc_graph *U) {
     cudaFree(U->tasks);
     cudaFree(U->qhead);
     cudaFree(U->status);
+    cudaFree(U->racc);
     vdmc_hub_free(U);
     if (U->side) cudaStreamDestroy(U->side);
     if (U->ev_fork) cudaEventDestroy(U->ev_fork);

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         atomicAdd(&hist_b[cls], 1ull);
                         credit(g, out, G.new2old, c, C, cls);
                     }
-                    flush_hist(g, hist_b, C, out, __ldg(G.new2old + b), lane);
+                    flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
                 }
                 // (A2) b in N(a) \ N(r), b > r
                 for (int64_t xb = a_up; xb < a_end; xb++) {
@@ -251,13 +251,24 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         atomicAdd(&hist_b[cls], 1ull);
                         credit(g, out, G.new2old, c, C, cls);
                     }
-                    flush_hist(g, hist_b, C, out, __ldg(G.new2old + b), lane);
+                    flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
                 }
             }
-            flush_hist(g, hist_a, C, out, __ldg(G.new2old + a), lane);
+            flush_hist(g, hist_a, C, out, row_of(G.new2old, a), lane);
         }
-        flush_hist(g, hist_r, C, out, __ldg(G.new2old + r), lane);
+        flush_hist(g, hist_r, C, out, row_of(G.new2old, r), lane);
     }
+}
+
+// out[new2old[r]] = acc[r], one warp per row (coalesced row copies)
+__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const int32_t *__restrict__ new2old, int32_t n,
+                               int C, uint64_t *__restrict__ out) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int32_t o = __ldg(new2old + r);
+    if (o < 0 || o >= n) return;
+    for (int c = lane; c < C; c += 32) out[(int64_t)o * C + c] = acc[r * C + c];
 }
 
 // Algorithmic bytes of one count: the adjacency rows each method must read
@@ -380,8 +391,16 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, sch.hub_min_l, s);
         if (st != VDMC_OK) return st;
     }
-    if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
-    GraphDesc d{g->rowptr, g->col, g->pbeg, g->new2old, out, g->n, 0, g->nnz};
+    // Credits accumulate in a rank-space array owned by the graph (no id-map
+    // load in front of each atomic); one coalesced pass then writes every row
+    // to its original id in `out`.
+    if (!g->racc && g->n > 0) {
+        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
+        VDMC_CUDA_TRY(cudaMalloc((void **)&g->racc, sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES));
+    }
+    uint64_t *acc = g->racc;
+    if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
+    GraphDesc d{g->rowptr, g->col, g->pbeg, nullptr, acc, g->n, 0, g->nnz};
     if (g->nhubs > 0) {
         // the root-per-CTA kernel runs on the graph's side stream, overlapped
         // with the warp kernel; the caller's stream waits for both
@@ -389,13 +408,18 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         VDMC_CUDA_TRY(device_lut(k, &lut));
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
         VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vdmc_status st = vdmc_hub_launch(g, k, out, lut, lo, hi, sch.hub_blocks_per_sm, g->side);
+        vdmc_status st = vdmc_hub_launch(g, k, acc, lut, lo, hi, sch.hub_blocks_per_sm, g->side);
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
     }
     vdmc_status st = launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
     if (g->nhubs > 0) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
-    return st;
+    if (st != VDMC_OK) return st;
+    if (g->n > 0) {
+        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, g->new2old, g->n, C, out);
+        VDMC_CUDA_TRY(cudaGetLastError());
+    }
+    return VDMC_OK;
 }
 
 extern "C" vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {

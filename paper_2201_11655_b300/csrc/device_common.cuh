@@ -96,11 +96,18 @@ __device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t f
            ((fac >> 1) << 1) | (fbc >> 1);
 }
 
-// +1 for vertex (rank) v in column cls of its original-id row
+// Output row of vertex (rank) v: its original id through the id map, or v
+// itself when the kernel accumulates in rank space (map == nullptr; the
+// rows are permuted to original ids afterwards).
+__device__ __forceinline__ int32_t row_of(const int32_t *map, uint32_t v) {
+    return map ? __ldg(map + v) : (int32_t)v;
+}
+
+// +1 for vertex (rank) v in column cls of its output row
 __device__ __forceinline__ void credit(const Csr &g, uint64_t *out, const int32_t *new2old, uint32_t v, int C,
                                        uint32_t cls) {
     if (!in_bounds(g, v < g.n)) return;
-    const int32_t o = __ldg(new2old + v);
+    const int32_t o = row_of(new2old, v);
     if (!in_bounds(g, o >= 0 && o < g.n)) return;
     atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], 1ull);
 }

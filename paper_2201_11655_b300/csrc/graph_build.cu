@@ -199,6 +199,7 @@ void free_graph_buffers(vdmc_graph *g) {
     cudaFree(g->status);
     vdmc_hub_free(g);
     vdmc_batch_plan_free(g);
+    cudaFree(g->racc);
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
@@ -402,6 +403,7 @@ extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *i
     info->num_tasks = g->ntasks;
     info->num_hub_roots = g->nhubs;
     info->device_bytes += (int64_t)g->hub_scratch_bytes;
+    if (g->racc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES);
     return VDMC_OK;
 }
 

@@ -115,7 +115,7 @@ struct Sink {
 __device__ __forceinline__ void gadd(const Sink &A, uint32_t v, uint32_t cls, unsigned long long cnt, int C) {
     if (cnt == 0ull) return;
     if (!in_bounds(A.g, v < A.g.n && cls < (uint32_t)C)) return;
-    const int32_t o = __ldg(A.new2old + v);
+    const int32_t o = row_of(A.new2old, v);
     if (!in_bounds(A.g, o >= 0 && o < A.g.n)) return;
     atomicAdd((unsigned long long *)&A.out[(int64_t)o * C + cls], cnt);
 }
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 }
             }
             __syncwarp();
-            flush_hist(g, hv, C, A.out, __ldg(A.new2old + v), lane);
+            flush_hist(g, hv, C, A.out, row_of(A.new2old, v), lane);
         }
         __syncthreads();
 
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
 
         // ---- phase 7: root credit, reset the slot
         {
-            const int32_t orig = __ldg(A.new2old + r);
+            const int32_t orig = row_of(A.new2old, (uint32_t)r);
             for (int c = tid; c < C; c += HUB_THREADS) {
                 const unsigned long long v = rootP[c] / (K == 3 ? 2ull : 3ull) + rootD[c];
                 if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
@@ -977,7 +977,7 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *
     char *base = (char *)g->hub_scratch;
     HubArgs A;
     A.g = Csr{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
-    A.new2old = g->new2old;
+    A.new2old = nullptr;  // credits in rank space (see vdmc_count_internal)
     A.out = out;
     A.lut_g = lut;
     A.hubs = g->hubs;

@@ -61,6 +61,7 @@ struct vdmc_graph {
     uint64_t serial;             // creation number (identifies the graph in cached batch plans)
     int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
+    uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
 };
 
 // ---- status helpers ----
