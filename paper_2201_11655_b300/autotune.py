@@ -32,7 +32,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNED_PATH = os.path.join(HERE, "tuned_schedules.json")
 
-STAGE1 = ([{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (16, 32, 64, 128, 256, 1024) for b in (1, 2)] +
+STAGE1 = ([{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024) for b in (1, 2)] +
           [{"hub_min_l": 0, "hub_blocks_per_sm": 1}])
 STAGE2 = [{"a_chunk": a, "warps_per_block": w} for a in (4, 16, 64) for w in (4, 8)]
 
@@ -124,6 +124,8 @@ def main():
     p.add_argument("--batch", type=int, default=0, help="tune on a union of N small graphs instead")
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--out", default=TUNED_PATH)
+    p.add_argument("--hub-min-l", default=None, help="comma list: restrict stage 1 to these values")
+    p.add_argument("--skip-stage2", action="store_true")
     a = p.parse_args()
     vdmc.load()
     if a.batch:
@@ -135,7 +137,11 @@ def main():
         g = vdmc.graph_create(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
         m, name = len(s), a.workload
     t0 = time.time()
-    best, ms, timings = tune(g, a.k, reps=a.reps)
+    stage1 = STAGE1
+    if a.hub_min_l:
+        keep = {int(x) for x in a.hub_min_l.split(",")}
+        stage1 = [c for c in STAGE1 if c["hub_min_l"] in keep]
+    best, ms, timings = tune(g, a.k, stage1=stage1, stage2=[] if a.skip_stage2 else STAGE2, reps=a.reps)
     key = "k%d/%s" % (a.k, bucket(n, m))
     save_tuned(key, best, ms, {"workload": name, "n": n, "m": m, "timings_ms": timings,
                                "tuned_seconds": round(time.time() - t0, 1)}, a.out)
