@@ -112,7 +112,9 @@ vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const in
  *              vdmc_graph_create
  * Vertex x of graph i becomes vertex voff[i] + x of the union, with
  * voff[i] = ns[0] + ... + ns[i-1]; the union's total vertex count must be
- * < 2^30.  No k-set of the union spans two graphs (they are not connected),
+ * < 2^30.  The union's vertex order keeps each graph's vertices in one
+ * contiguous block, in that graph's own degree order, so the roots counted
+ * at the same time belong to the same graph and their credits stay local.  No k-set of the union spans two graphs (they are not connected),
  * so one vdmc_count on the union counts all graphs in one launch and graph
  * i's counts are rows voff[i] .. voff[i+1]-1 of the output.  A local id
  * outside [0, ns[i]) returns VDMC_ERR_OUT_OF_RANGE_VERTEX.  Synchronises

@@ -323,7 +323,7 @@ extern "C" vdmc_status vdmc_graph_create_batch(int32_t num, const int32_t *ns, c
     vdmc_status st = VDMC_OK;
     if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
     else if (hbad) st = VDMC_ERR_OUT_OF_RANGE_VERTEX;
-    else st = vdmc_graph_create((int32_t)N, M, a, b, 1, stream, out);
+    else st = vdmc_graph_create_grouped((int32_t)N, M, a, b, 1, stream, out, voff_d, num);
     cudaFree(a);
     cudaFree(b);
     cudaFree(voff_d);

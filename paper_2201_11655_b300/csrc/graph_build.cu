@@ -110,9 +110,26 @@ __global__ void max_degree(const int32_t *deg, int32_t n, int *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
-__global__ void rank_keys(const int32_t *deg, int32_t n, const int *dmax, uint64_t *keys) {
+// Sort key of vertex v: (group, max_degree - degree, id).  Without groups
+// (a single graph) the order is the paper's degree order; with groups (a
+// batch of graphs) each graph's vertices form one contiguous block of ranks,
+// in that graph's own degree order, so roots counted at the same time come
+// from the same graph and their credits stay in a small region.
+__global__ void rank_keys(const int32_t *deg, int32_t n, const int *dmax, const int64_t *goff, int32_t ngroups,
+                          int dbits, uint64_t *keys) {
     int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) keys[v] = ((uint64_t)(uint32_t)(*dmax - deg[v]) << 32) | (uint32_t)v;
+    if (v >= n) return;
+    uint64_t grp = 0;
+    if (goff) {
+        int lo = 0, hi = ngroups;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (goff[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        grp = (uint64_t)lo;
+    }
+    keys[v] = (grp << (32 + dbits)) | ((uint64_t)(uint32_t)(*dmax - deg[v]) << 32) | (uint32_t)v;
 }
 
 __global__ void rank_maps(const uint64_t *sorted, int32_t n, const int32_t *deg, int32_t *new2old,
@@ -206,7 +223,7 @@ void free_graph_buffers(vdmc_graph *g) {
 }
 
 vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int on_device,
-                        cudaStream_t s, vdmc_graph *g) {
+                        cudaStream_t s, vdmc_graph *g, const int64_t *goff, int32_t ngroups) {
     g->n = n;
     g->info.n = n;
     g->info.arcs_in = m;
@@ -306,13 +323,19 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     }
     if (n > 0) {
         max_degree<<<blocks_for(n, 256), 256, 0, s>>>(deg, n, dmax);
-        rank_keys<<<blocks_for(n, 256), 256, 0, s>>>(deg, n, dmax, rk);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     int hdmax = 0;
     VDMC_CUDA_TRY(cudaMemcpyAsync(&hdmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
     VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-    VDMC_CUDA_TRY(vdmc_radix_sort_u64(rk, rk2, n, 32, 32 + bits_for((uint64_t)hdmax), s, &rsorted));
+    const int dbits = bits_for((uint64_t)hdmax);
+    const int gbits = goff ? bits_for((uint64_t)(ngroups > 0 ? ngroups - 1 : 0)) : 0;
+    if (32 + dbits + gbits > 64) return VDMC_ERR_INVALID_ARG;
+    if (n > 0) {
+        rank_keys<<<blocks_for(n, 256), 256, 0, s>>>(deg, n, dmax, goff, ngroups, dbits, rk);
+        VDMC_CUDA_TRY(cudaGetLastError());
+    }
+    VDMC_CUDA_TRY(vdmc_radix_sort_u64(rk, rk2, n, 32, 32 + dbits + gbits, s, &rsorted));
     if (n > 0) {
         rank_maps<<<blocks_for(n, 256), 256, 0, s>>>(rsorted, n, deg, g->new2old, g->old2new, deg_rank);
         VDMC_CUDA_TRY(cudaGetLastError());
@@ -359,8 +382,20 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
 
 }  // namespace
 
+vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                      int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
+                                      int32_t ngroups);
+
 extern "C" vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                          int ptrs_on_device, void *stream, vdmc_graph **out) {
+    return vdmc_graph_create_grouped(n, m, src, dst, ptrs_on_device, stream, out, nullptr, 0);
+}
+
+// goff: device int64[ngroups + 1] vertex offsets of the graphs of a batch,
+// or nullptr for a single graph
+vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                      int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
+                                      int32_t ngroups) {
     if (!out) return VDMC_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 0 || n >= (1 << 30) || m < 0 || m > 0xffffffffll) return VDMC_ERR_INVALID_ARG;
@@ -369,7 +404,7 @@ extern "C" vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *sr
     if (!g) return VDMC_ERR_OOM;
     std::memset(g, 0, sizeof *g);
     cudaStream_t s = (cudaStream_t)stream;
-    vdmc_status st = create_impl(n, m, src, dst, ptrs_on_device, s, g);
+    vdmc_status st = create_impl(n, m, src, dst, ptrs_on_device, s, g, goff, ngroups);
     if (st != VDMC_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();

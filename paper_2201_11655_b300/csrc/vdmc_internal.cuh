@@ -96,6 +96,11 @@ const uint16_t *vdmc_host_canon(int k, int *num_classes);
 vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s);
 cudaError_t vdmc_device_lut(int k, const uint8_t **out);
 
+// ---- graph build (graph_build.cu) ----
+vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                      int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
+                                      int32_t ngroups);
+
 // ---- batch plans (batch.cu) ----
 void vdmc_batch_plan_free(vdmc_graph *g);
 uint64_t vdmc_next_serial();
