@@ -51,6 +51,9 @@ namespace {
 constexpr int HUB_WARPS = 16;
 constexpr int HUB_THREADS = HUB_WARPS * 32;
 constexpr int32_t CLAIMED = -2;  // posmap: claimed, index being written
+// largest P bitmap kept in shared memory (next to ~37 KB of static shared
+// memory): 46,000 words = 184 KB, i.e. graphs of up to 1,472,000 vertices
+constexpr int64_t HUB_SMEM_BITS_MAX_WORDS = 46000;
 
 struct HubArgs {
     Csr g;
@@ -71,6 +74,8 @@ struct HubArgs {
     uint32_t *hcx;     // lmax * 3 per slot: |NH(x)| by colour
     uint32_t *wx;      // lmax * 3 per slot: |NQ(x)| by flag
     uint32_t *htx;     // lmax * 9 per slot: |NH(x)| by (colour, flag)
+    uint32_t *tbits;   // (n + 31) / 32 words per slot: bit set = Q vertex already claimed
+    int32_t pbits_words;  // > 0: membership of P as a bitmap in shared memory
     int32_t *npoff;    // tcap + 1 per slot: offsets of the NP lists
     uint32_t *nplist;  // npcap per slot: (position << 2) | h(x, b)
     int64_t tcap, hcap, lmax, npcap;
@@ -159,12 +164,18 @@ __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *
     __syncthreads();
 }
 
-// return the slot to its resting state (posmap -1, counters 0)
+// return the slot to its resting state (posmap -1, counters and bits 0)
 __device__ void reset_slot(int32_t *posmap, uint32_t *qcnt, const int32_t *touched, const uint32_t *P, int32_t L,
-                           int32_t tcount) {
-    for (int32_t p = threadIdx.x; p < L; p += HUB_THREADS) posmap[__ldg(P + p) >> 2] = -1;
+                           int32_t tcount, uint32_t *pbits, bool sbits, uint32_t *tbits) {
+    for (int32_t p = threadIdx.x; p < L; p += HUB_THREADS) {
+        const uint32_t u = __ldg(P + p) >> 2;
+        posmap[u] = -1;
+        if (sbits) pbits[u >> 5] = 0u;
+    }
     for (int32_t t = threadIdx.x; t < tcount; t += HUB_THREADS) {
-        posmap[touched[t]] = -1;
+        const int32_t u = touched[t];
+        posmap[u] = -1;
+        tbits[u >> 5] = 0u;
         for (int k = 0; k < 9; k++) qcnt[(int64_t)t * 9 + k] = 0u;
     }
 }
@@ -205,10 +216,21 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     uint32_t *wx = A.wx + slot * A.lmax * 3;
     uint32_t *htx = A.htx + slot * A.lmax * 9;
     int32_t *npoff = A.npoff + slot * (A.tcap + 1);
+    uint32_t *tbits = A.tbits + slot * (int64_t)((g.n + 31) / 32);
+    // P membership: a bit per vertex in shared memory (when n fits), else
+    // the position map; "claimed Q vertex": a bit per vertex per slot (small
+    // enough to stay in L2, unlike the position map)
+    extern __shared__ uint32_t pbits[];
+    const bool sbits = A.pbits_words > 0;
+    auto in_P = [&](uint32_t u) -> bool {
+        return sbits ? ((pbits[u >> 5] >> (u & 31u)) & 1u) != 0u : __ldcg(posmap + u) >= 0;
+    };
+    auto claimed = [&](uint32_t u) -> bool { return ((__ldcg(tbits + (u >> 5)) >> (u & 31u)) & 1u) != 0u; };
     uint32_t *nplist = A.nplist + slot * A.npcap;
     unsigned long long *hv = whist[warp];
 
     for (int i = tid; i < NIDX; i += HUB_THREADS) lut[i] = A.lut_g[i];
+    for (int i = tid; i < A.pbits_words; i += HUB_THREADS) pbits[i] = 0u;
     for (int i = tid; i < HUB_WARPS * C; i += HUB_THREADS) (&whist[0][0])[i] = 0ull;
 
     for (;;) {
@@ -239,6 +261,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         for (int32_t p = tid; p < L; p += HUB_THREADS) {
             const uint32_t e = __ldg(P + p);
             posmap[e >> 2] = p;
+            if (sbits) atomicOr(&pbits[(e >> 2) >> 5], 1u << ((e >> 2) & 31u));
             atomicAdd(&ncol[(e & 3u) - 1u], 1u);
         }
         __syncthreads();
@@ -257,8 +280,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 for (int64_t e = xu + (coop ? lane : 0); e < xe; e += coop ? 32 : 1) {
                     const uint32_t ent = __ldg(g.col + e);
                     const uint32_t u = ent >> 2, f = ent & 3u;
-                    const int32_t p = __ldcg(posmap + u);
-                    if (p >= 0) {
+                    if (in_P(u)) {
+                        const int32_t p = __ldcg(posmap + u);
                         dh++;
                         const uint32_t cu = __ldg(P + p) & 3u;
                         hc0 += cu == 1u;
@@ -268,12 +291,13 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         w0 += f == 1u;
                         w1 += f == 2u;
                         w2 += f == 3u;
-                        if (p == -1 && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
+                        if (!claimed(u) && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
                             const int32_t t = atomicAdd(&s_tcount, 1);
                             if (in_bounds(g, t < A.tcap)) {
                                 touched[t] = (int32_t)u;
                                 posmap[u] = -3 - t;
                             }
+                            atomicOr(tbits + (u >> 5), 1u << (u & 31u));
                         }
                     }
                 }
@@ -297,7 +321,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         cta_scan(hptr, L, warp_sums, &s_total);
         if (!in_bounds(g, s_total <= A.hcap && s_skip == 0)) {
             // leave the slot clean before giving up on this root
-            reset_slot(posmap, qcnt, touched, P, L, min(tcount, (int32_t)A.tcap));
+            reset_slot(posmap, qcnt, touched, P, L, min(tcount, (int32_t)A.tcap), pbits, sbits, tbits);
             continue;
         }
 
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         __syncthreads();
         cta_scan(npoff, tcount, warp_sums, &s_total);
         if (!in_bounds(g, s_total <= A.npcap)) {
-            reset_slot(posmap, qcnt, touched, P, L, tcount);
+            reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
             continue;
         }
         for (int pass = 0; pass < 2; pass++) {
@@ -377,15 +401,15 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     const int64_t e = e0 + (coop ? lane : 0);
                     const bool valid = e < be;
                     const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
-                    const int32_t p = valid ? __ldcg(posmap + (ent >> 2)) : -1;
-                    const bool isP = valid && p >= 0;
+                    const bool isP = valid && in_P(ent >> 2);
                     const uint32_t bal = coop ? __ballot_sync(0xffffffffu, isP) : (isP ? 1u : 0u);
                     if (isP) {
+                        const int32_t p = __ldcg(posmap + (ent >> 2));
                         const int32_t idx = base + (coop ? __popc(bal & lt) : 0);
                         if (in_bounds(g, idx < lim)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
                     }
                     base += __popc(bal);
-                    if (valid && p < 0) {
+                    if (valid && !isP) {
                         const uint32_t f = ent & 3u;
                         c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
                     }
@@ -539,8 +563,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r) + ls; e < ue; e += st) {
                             const uint32_t ec = __ldg(g.col + e);
                             const uint32_t c = ec >> 2;
+                            if (in_P(c)) continue;
                             const int32_t pc = __ldcg(posmap + c);
-                            if (pc >= 0) continue;
                             if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
                             const int64_t tc = -3 - (int64_t)pc;
                             const uint32_t fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
@@ -755,12 +779,12 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             for (int64_t e = bu + ls; e < be; e += st) {
                 const uint32_t ent = __ldg(g.col + e);
                 const uint32_t c = ent >> 2;
-                const int32_t pc = __ldcg(posmap + c);
-                if (pc >= 0) continue;
+                if (in_P(c)) continue;
                 const uint32_t gg = ent & 3u;
                 for (int k = 0; k < 9; k++)
                     if (q[k]) gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], q[k], C);
-                if (pc == -1 || c <= b) continue;  // no P neighbour, or counted from c
+                if (c <= b || !claimed(c)) continue;  // counted from c, or no P neighbour
+                const int32_t pc = __ldcg(posmap + c);
                 if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
                 const int64_t t2 = -3 - (int64_t)pc;
                 const int32_t p0 = npoff[t2], p1 = npoff[t2 + 1];
@@ -804,7 +828,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
             }
         }
-        reset_slot(posmap, qcnt, touched, P, L, tcount);
+        reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
     }
 }
 
@@ -920,7 +944,7 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
 namespace {
 
 struct HubLayout {
-    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npoff, nplist, total;
+    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npoff, nplist, tbits, total;
 };
 
 HubLayout hub_layout(const vdmc_graph *g, int slots) {
@@ -938,6 +962,7 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
     L.htx = o; o += align256(S * lm * 9 * 4);
     L.npoff = o; o += align256(S * (t + 1) * 4);
     L.nplist = o; o += align256(S * (size_t)g->hub_npcap * 4);
+    L.tbits = o; o += align256(S * ((n + 31) / 32) * 4);
     L.total = o;
     return L;
 }
@@ -965,6 +990,7 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *
         if (!g->hub_qhead) VDMC_CUDA_TRY(cudaMalloc((void **)&g->hub_qhead, sizeof(unsigned long long)));
         char *base = (char *)g->hub_scratch;
         VDMC_CUDA_TRY(cudaMemsetAsync(base + L.qcnt, 0, L.wq - L.qcnt, s));
+        VDMC_CUDA_TRY(cudaMemsetAsync(base + L.tbits, 0, L.total - L.tbits, s));
         const int64_t np = (int64_t)slots * g->n;
         if (np > 0) {
             fill_i32<<<(unsigned)((np + 255) / 256), 256, 0, s>>>((int32_t *)(base + L.posmap), np, -1);
@@ -997,12 +1023,21 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *
     A.npoff = (int32_t *)(base + L.npoff);
     A.nplist = (uint32_t *)(base + L.nplist);
     A.npcap = g->hub_npcap;
+    A.tbits = (uint32_t *)(base + L.tbits);
+    const int64_t words = ((int64_t)g->n + 31) / 32;
+    A.pbits_words = words <= HUB_SMEM_BITS_MAX_WORDS ? (int32_t)words : 0;
+    const size_t dsmem = (size_t)A.pbits_words * 4;
     A.tcap = g->hub_tcap;
     A.hcap = g->hub_hcap;
     A.lmax = g->hub_lmax;
     VDMC_CUDA_TRY(cudaMemsetAsync(g->hub_qhead, 0, sizeof(unsigned long long), s));
-    if (k == 3) hub_kernel<3><<<(unsigned)slots, HUB_THREADS, 0, s>>>(A);
-    else hub_kernel<4><<<(unsigned)slots, HUB_THREADS, 0, s>>>(A);
+    if (k == 3) {
+        VDMC_CUDA_TRY(cudaFuncSetAttribute(hub_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        hub_kernel<3><<<(unsigned)slots, HUB_THREADS, dsmem, s>>>(A);
+    } else {
+        VDMC_CUDA_TRY(cudaFuncSetAttribute(hub_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        hub_kernel<4><<<(unsigned)slots, HUB_THREADS, dsmem, s>>>(A);
+    }
     VDMC_CUDA_TRY(cudaGetLastError());
     return VDMC_OK;
 }
