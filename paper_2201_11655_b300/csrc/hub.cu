@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     __shared__ unsigned long long Etype[27];
     __shared__ unsigned long long Wtot[9];
     __shared__ uint32_t ncol[3];
-    __shared__ int32_t s_root, s_tcount, s_total, s_skip;
+    __shared__ int32_t s_root, s_tcount, s_total, s_skip, s_chunk;
     __shared__ int32_t warp_sums[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             s_root = q < (unsigned long long)A.nhubs ? A.hubs[q] : -1;
             s_tcount = 0;
             s_skip = 0;
+            s_chunk = 0;
         }
         for (int i = tid; i < C; i += HUB_THREADS) {
             rootP[i] = 0ull;
@@ -733,90 +734,147 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         }
         __syncthreads();
 
-        // ---- phase 6: per Q vertex b
-        // light b (short row, few P neighbours): one per thread; heavy b: one
-        // per warp
-        for (int pass = 0; pass < 2; pass++) {
-          const bool coop = pass == 1;
-          const int32_t ls = coop ? lane : 0, st = coop ? 32 : 1;
-          for (int32_t t = coop ? warp : tid; t < tcount; t += coop ? HUB_WARPS : HUB_THREADS) {
-            const uint32_t b = (uint32_t)touched[t];
-            const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
-            const int32_t o0 = npoff[t], o1 = npoff[t + 1];
-            if ((be - bb > 32 || o1 - o0 > 16) != coop) continue;
-            uint32_t q[9];
-            for (int k = 0; k < 9; k++) q[k] = __ldcg(qcnt + (int64_t)t * 9 + k);
-            const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-            if (K == 3) {
-                // path with b at depth 2: by (colour, flag) of its P neighbours
-                for (int k = ls; k < 9; k += st) {
-                    const uint32_t cls = lut[mask3((uint32_t)(k / 3 + 1), 0u, (uint32_t)(k % 3 + 1))];
-                    gadd(S, b, cls, q[k], C);
-                }
-                continue;
-            }
-            // S4 credit of b: P neighbours x by (colour, h(x,b)), Q neighbours by flag
-            for (int k27 = ls; k27 < 27; k27 += st) {
-                const int k = k27 / 3, g3 = k27 % 3;
-                const uint32_t cls = lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, (uint32_t)g3 + 1)];
-                gadd(S, b, cls, (unsigned long long)q[k] * wq[(int64_t)t * 3 + g3], C);
-            }
-            // S2 with b adjacent to two members x, y of P, counted as if x, y
-            // were not adjacent (H-adjacent pairs are corrected per H-edge):
-            // pairs of NP(b) by the (colour, h(., b)) types of their members
-            for (int pr = ls; pr < 81; pr += st) {
-                const int t1 = pr / 9, t2 = pr % 9;
-                if (t1 > t2) continue;
-                const unsigned long long cnt = t1 < t2 ? (unsigned long long)q[t1] * q[t2]
-                                                       : (unsigned long long)q[t1] * (q[t1] - (q[t1] ? 1u : 0u)) / 2;
-                const uint32_t cls = lut[mask4((uint32_t)(t1 / 3 + 1), (uint32_t)(t2 / 3 + 1), 0u, 0u,
-                                               (uint32_t)(t1 % 3 + 1), (uint32_t)(t2 % 3 + 1))];
-                gadd(S, b, cls, cnt, C);
-                sadd(rootD, cls, cnt);
-            }
-            // S4 credit of each c in NQ(b); triangles v - b - c2 with c2 in
-            // NQ(b), b < c2: enumerate the S3 set and correct the bulk counts
-            for (int64_t e = bu + ls; e < be; e += st) {
-                const uint32_t ent = __ldg(g.col + e);
-                const uint32_t c = ent >> 2;
-                if (in_P(c)) continue;
-                const uint32_t gg = ent & 3u;
-                for (int k = 0; k < 9; k++)
-                    if (q[k]) gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], q[k], C);
-                if (c <= b || !claimed(c)) continue;  // counted from c, or no P neighbour
-                const int32_t pc = __ldcg(posmap + c);
-                if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
-                const int64_t t2 = -3 - (int64_t)pc;
-                const int32_t p0 = npoff[t2], p1 = npoff[t2 + 1];
-                const bool short_b = (o1 - o0) <= (p1 - p0);
-                const int32_t s0 = short_b ? o0 : p0, s1 = short_b ? o1 : p1;
-                for (int32_t x = s0; x < s1; x++) {
-                    const uint32_t ex = nplist[x];
-                    const uint32_t vp = ex >> 2;
-                    const uint32_t fo = short_b ? hlist_find(nplist, p0, p1, vp) : hlist_find(nplist, o0, o1, vp);
-                    if (!fo) continue;
-                    const uint32_t fvb = short_b ? (ex & 3u) : fo;    // h(v, b)
-                    const uint32_t fvc = short_b ? fo : (ex & 3u);    // h(v, c)
-                    const uint32_t cv = __ldg(P + vp) & 3u;
-                    const uint32_t vv = __ldg(P + vp) >> 2;
-                    const uint32_t clE = lut[mask4(cv, 0u, 0u, fvb, fvc, gg)];
-                    const uint32_t clF = lut[mask4(cv, 0u, 0u, fvb, fvc, 0u)];
-                    const uint32_t clA = lut[mask4(cv, 0u, 0u, fvb, 0u, gg)];
-                    const uint32_t clB = lut[mask4(cv, 0u, 0u, fvc, 0u, swapf(gg))];
-                    const uint32_t who[3] = {vv, b, c};
-                    for (int m = 0; m < 3; m++) {
-                        gadd(S, who[m], clE, 1ull, C);
-                        gadd(S, who[m], clF, ~0ull, C);
-                        gadd(S, who[m], clA, ~0ull, C);
-                        gadd(S, who[m], clB, ~0ull, C);
+        // ---- phase 6: per Q vertex b.  A warp takes a chunk of 32 Q
+        // vertices (claimed dynamically); each lane first credits its own b,
+        // then the warp walks the concatenated upper rows of the chunk with
+        // its lanes on consecutive entries, so long and short rows alike keep
+        // the lanes busy.
+        {
+            // [32][9] P-neighbour counts of the chunk's Q vertices, in the warp's
+            // histogram (k = 4 only; k = 3 credits b directly)
+            static_assert(K == 3 || 2 * C >= 32 * 9, "chunk counts must fit the warp histogram");
+            uint32_t *sq = reinterpret_cast<uint32_t *>(hv);
+            for (;;) {
+                int32_t c0 = 0;
+                if (lane == 0) c0 = atomicAdd(&s_chunk, 32);
+                c0 = __shfl_sync(0xffffffffu, c0, 0);
+                if (c0 >= tcount) break;
+                const int32_t t = c0 + lane;
+                uint32_t b = 0u, nzm = 0u;
+                int64_t be = 0;
+                int32_t len = 0, o0 = 0, o1 = 0;
+                if (t < tcount) {
+                    b = (uint32_t)touched[t];
+                    const int64_t bb = __ldg(g.rowptr + b);
+                    be = __ldg(g.rowptr + b + 1);
+                    len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
+                    o0 = npoff[t];
+                    o1 = npoff[t + 1];
+#pragma unroll
+                    for (int k = 0; k < 9; k++) {
+                        const uint32_t qk = __ldcg(qcnt + (int64_t)t * 9 + k);
+                        if (K == 3) {
+                            // path with b at depth 2: by (colour, flag) of its P neighbours
+                            gadd(S, b, lut[mask3((uint32_t)(k / 3 + 1), 0u, (uint32_t)(k % 3 + 1))], qk, C);
+                        } else {
+                            sq[lane * 9 + k] = qk;
+                            nzm |= (qk != 0u ? 1u : 0u) << k;
+                        }
                     }
-                    sadd(rootD, clE, 1ull);
-                    sadd(rootD, clF, ~0ull);
-                    sadd(rootD, clA, ~0ull);
-                    sadd(rootD, clB, ~0ull);
+                    if (K == 4) {
+                        uint32_t w3[3];
+#pragma unroll
+                        for (int f = 0; f < 3; f++) w3[f] = wq[(int64_t)t * 3 + f];
+                        for (uint32_t m1 = nzm; m1; m1 &= m1 - 1u) {
+                            const int t1 = __ffs(m1) - 1;
+                            const unsigned long long q1 = sq[lane * 9 + t1];
+                            const uint32_t c1 = (uint32_t)(t1 / 3 + 1), h1 = (uint32_t)(t1 % 3 + 1);
+                            // S4 credit of b: P neighbours x by (colour, h(x,b)), Q
+                            // neighbours by flag
+#pragma unroll
+                            for (int f = 0; f < 3; f++)
+                                gadd(S, b, lut[mask4(c1, 0u, 0u, h1, 0u, (uint32_t)f + 1)], q1 * w3[f], C);
+                            // S2 with b adjacent to two members x, y of P, counted as
+                            // if x, y were not adjacent (H-adjacent pairs are
+                            // corrected per H-edge): pairs of NP(b) by type
+                            {
+                                const unsigned long long cnt = q1 * (q1 - 1ull) / 2ull;
+                                const uint32_t cls = lut[mask4(c1, c1, 0u, 0u, h1, h1)];
+                                gadd(S, b, cls, cnt, C);
+                                sadd(rootD, cls, cnt);
+                            }
+                            for (uint32_t m2 = m1 & (m1 - 1u); m2; m2 &= m2 - 1u) {
+                                const int t2 = __ffs(m2) - 1;
+                                const unsigned long long cnt = q1 * sq[lane * 9 + t2];
+                                const uint32_t cls = lut[mask4(c1, (uint32_t)(t2 / 3 + 1), 0u, 0u, h1, (uint32_t)(t2 % 3 + 1))];
+                                gadd(S, b, cls, cnt, C);
+                                sadd(rootD, cls, cnt);
+                            }
+                        }
+                    }
                 }
+                if (K == 3) continue;
+                __syncwarp();
+                int32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int32_t base = 0; base < total; base += 32) {
+                    const int32_t j = base + lane;
+                    // owner lane w: the first lane whose inclusive sum exceeds j
+                    int32_t w = 0;
+#pragma unroll
+                    for (int sh = 16; sh >= 1; sh >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                    const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
+                    const int64_t beo = __shfl_sync(0xffffffffu, be, w);
+                    const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                    const uint32_t nzo = __shfl_sync(0xffffffffu, nzm, w);
+                    const int32_t oo0 = __shfl_sync(0xffffffffu, o0, w), oo1 = __shfl_sync(0xffffffffu, o1, w);
+                    if (j >= total) continue;
+                    const int64_t e = beo - (int64_t)(io - j);  // entries of b end at be
+                    const uint32_t ent = __ldg(g.col + e);
+                    const uint32_t c = ent >> 2;
+                    if (in_P(c)) continue;
+                    const uint32_t gg = ent & 3u;
+                    // S4 credit of c (b at depth 2, c at depth 3)
+#pragma unroll
+                    for (int k = 0; k < 9; k++)
+                        if ((nzo >> k) & 1u)
+                            gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], sq[w * 9 + k], C);
+                    // triangles v - b - c with c in NQ(b), b < c: enumerate the
+                    // S3 set and correct the bulk counts
+                    if (c <= bo || !claimed(c)) continue;  // counted from c, or no P neighbour
+                    const int32_t pc = __ldcg(posmap + c);
+                    if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                    const int64_t t2 = -3 - (int64_t)pc;
+                    const int32_t p0 = npoff[t2], p1 = npoff[t2 + 1];
+                    const bool short_b = (oo1 - oo0) <= (p1 - p0);
+                    const int32_t s0 = short_b ? oo0 : p0, s1 = short_b ? oo1 : p1;
+                    for (int32_t x = s0; x < s1; x++) {
+                        const uint32_t ex = nplist[x];
+                        const uint32_t vp = ex >> 2;
+                        const uint32_t fo = short_b ? hlist_find(nplist, p0, p1, vp) : hlist_find(nplist, oo0, oo1, vp);
+                        if (!fo) continue;
+                        const uint32_t fvb = short_b ? (ex & 3u) : fo;    // h(v, b)
+                        const uint32_t fvc = short_b ? fo : (ex & 3u);    // h(v, c)
+                        const uint32_t pv = __ldg(P + vp);
+                        const uint32_t cv = pv & 3u, vv = pv >> 2;
+                        const uint32_t clE = lut[mask4(cv, 0u, 0u, fvb, fvc, gg)];
+                        const uint32_t clF = lut[mask4(cv, 0u, 0u, fvb, fvc, 0u)];
+                        const uint32_t clA = lut[mask4(cv, 0u, 0u, fvb, 0u, gg)];
+                        const uint32_t clB = lut[mask4(cv, 0u, 0u, fvc, 0u, swapf(gg))];
+                        const uint32_t who[3] = {vv, bo, c};
+#pragma unroll
+                        for (int m = 0; m < 3; m++) {
+                            gadd(S, who[m], clE, 1ull, C);
+                            gadd(S, who[m], clF, ~0ull, C);
+                            gadd(S, who[m], clA, ~0ull, C);
+                            gadd(S, who[m], clB, ~0ull, C);
+                        }
+                        sadd(rootD, clE, 1ull);
+                        sadd(rootD, clF, ~0ull);
+                        sadd(rootD, clA, ~0ull);
+                        sadd(rootD, clB, ~0ull);
+                    }
+                }
+                __syncwarp();
             }
-          }
+            __syncwarp();
+            for (int c = lane; c < C; c += 32) hv[c] = 0ull;  // the chunk area is the warp's histogram
         }
         __syncthreads();
 
