@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     __shared__ unsigned long long Etype[27];
     __shared__ unsigned long long Wtot[9];
     __shared__ uint32_t ncol[3];
-    __shared__ int32_t s_root, s_tcount, s_total, s_skip, s_chunk;
+    __shared__ int32_t s_root, s_tcount, s_total, s_skip, s_chunk, s_chunk4;
     __shared__ int32_t warp_sums[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             s_tcount = 0;
             s_skip = 0;
             s_chunk = 0;
+            s_chunk4 = 0;
         }
         for (int i = tid; i < C; i += HUB_THREADS) {
             rootP[i] = 0ull;
@@ -377,54 +378,90 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
 
         // ---- phase 4: NP(b) lists (P-neighbours of each Q vertex b, in
         // position order, read from b's own row) and |NQ(b)| by flag
-        for (int32_t t = tid; t < tcount; t += HUB_THREADS) {
-            uint32_t s9 = 0;
-            for (int k = 0; k < 9; k++) s9 += __ldcg(qcnt + (int64_t)t * 9 + k);
-            npoff[t] = (int32_t)s9;
-        }
-        __syncthreads();
-        cta_scan(npoff, tcount, warp_sums, &s_total);
-        if (!in_bounds(g, s_total <= A.npcap)) {
-            reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
-            continue;
-        }
-        for (int pass = 0; pass < 2; pass++) {
-            const bool coop = pass == 1;
-            for (int32_t t = coop ? warp : tid; t < tcount; t += coop ? HUB_WARPS : HUB_THREADS) {
-                const uint32_t b = (uint32_t)touched[t];
-                const int64_t bb = __ldg(g.rowptr + b), be = __ldg(g.rowptr + b + 1);
-                if ((be - bb > 32) != coop) continue;
-                const int64_t bu = upper_row(g.col, bb, be, (uint32_t)r);
-                int32_t base = npoff[t];
-                const int32_t lim = npoff[t + 1];
-                uint32_t c0 = 0, c1 = 0, c2 = 0;
-                for (int64_t e0 = bu; e0 < be; e0 += coop ? 32 : 1) {
-                    const int64_t e = e0 + (coop ? lane : 0);
-                    const bool valid = e < be;
-                    const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
-                    const bool isP = valid && in_P(ent >> 2);
-                    const uint32_t bal = coop ? __ballot_sync(0xffffffffu, isP) : (isP ? 1u : 0u);
-                    if (isP) {
-                        const int32_t p = __ldcg(posmap + (ent >> 2));
-                        const int32_t idx = base + (coop ? __popc(bal & lt) : 0);
-                        if (in_bounds(g, idx < lim)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
-                    }
-                    base += __popc(bal);
-                    if (valid && !isP) {
-                        const uint32_t f = ent & 3u;
-                        c0 += f == 1u; c1 += f == 2u; c2 += f == 3u;
-                    }
-                }
-                if (coop) {
-                    c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
-                }
-                if (!coop || lane == 0) {
-                    in_bounds(g, base == lim);
-                    wq[(int64_t)t * 3 + 0] = c0; wq[(int64_t)t * 3 + 1] = c1; wq[(int64_t)t * 3 + 2] = c2;
-                }
+        if constexpr (K == 4) {  // k = 3 needs neither NP lists nor |NQ(b)|
+            for (int32_t t = tid; t < tcount; t += HUB_THREADS) {
+                uint32_t s9 = 0;
+                for (int k = 0; k < 9; k++) s9 += __ldcg(qcnt + (int64_t)t * 9 + k);
+                npoff[t] = (int32_t)s9;
             }
+            __syncthreads();
+            cta_scan(npoff, tcount, warp_sums, &s_total);
+            if (!in_bounds(g, s_total <= A.npcap)) {
+                reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
+                continue;
+            }
+            // a warp takes a chunk of 32 Q vertices and walks their concatenated
+            // upper rows, lanes on consecutive entries; P-neighbours go to NP(b) in
+            // row (= position) order, the others are counted by flag
+            {
+                // per lane of the chunk: entries of NP(b) written so far, |NQ(b)| by
+                // flag (in the warp's histogram, zero again before phase 5)
+                static_assert(2 * C >= 32 * 4, "chunk counters must fit the warp histogram");
+                uint32_t *srun = reinterpret_cast<uint32_t *>(hv);
+                uint32_t *swq = srun + 32;
+                for (;;) {
+                    int32_t c0 = 0;
+                    if (lane == 0) c0 = atomicAdd(&s_chunk4, 32);
+                    c0 = __shfl_sync(0xffffffffu, c0, 0);
+                    if (c0 >= tcount) break;
+                    const int32_t t = c0 + lane;
+                    int64_t be = 0;
+                    int32_t len = 0, nb0 = 0;
+                    if (t < tcount) {
+                        const uint32_t b = (uint32_t)touched[t];
+                        const int64_t bb = __ldg(g.rowptr + b);
+                        be = __ldg(g.rowptr + b + 1);
+                        len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
+                        nb0 = npoff[t];
+                    }
+                    srun[lane] = 0u;
+                    swq[lane * 3 + 0] = swq[lane * 3 + 1] = swq[lane * 3 + 2] = 0u;
+                    int32_t incl = len;
+    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    __syncwarp();
+                    for (int32_t base = 0; base < total; base += 32) {
+                        const int32_t j = base + lane;
+                        int32_t w = 0;
+    #pragma unroll
+                        for (int sh = 16; sh >= 1; sh >>= 1)
+                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                        const int64_t beo = __shfl_sync(0xffffffffu, be, w);
+                        const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                        const int32_t nbo = __shfl_sync(0xffffffffu, nb0, w);
+                        const bool valid = j < total;
+                        const uint32_t ent = valid ? __ldg(g.col + (beo - (int64_t)(io - j))) : 0u;
+                        const bool isP = valid && in_P(ent >> 2);
+                        // lanes of the same Q vertex in this window (idle lanes apart)
+                        const uint32_t grp = __match_any_sync(0xffffffffu, valid ? w : 32 + lane);
+                        const uint32_t bal = __ballot_sync(0xffffffffu, isP) & grp;
+                        const uint32_t before = srun[w];
+                        if (isP) {
+                            const int32_t p = __ldcg(posmap + (ent >> 2));
+                            const int64_t idx = (int64_t)nbo + before + __popc(bal & lt);
+                            if (in_bounds(g, idx < A.npcap)) nplist[idx] = ((uint32_t)p << 2) | swapf(ent & 3u);  // h(x, b)
+                        } else if (valid && in_bounds(g, (ent & 3u) != 0u)) {
+                            atomicAdd(&swq[w * 3 + (ent & 3u) - 1u], 1u);
+                        }
+                        __syncwarp();
+                        if (valid && lane == __ffs(grp) - 1) srun[w] = before + __popc(bal);
+                        __syncwarp();
+                    }
+                    if (t < tcount) {
+                        in_bounds(g, (int32_t)srun[lane] == npoff[t + 1] - nb0);
+    #pragma unroll
+                        for (int f = 0; f < 3; f++) wq[(int64_t)t * 3 + f] = swq[lane * 3 + f];
+                    }
+                    __syncwarp();
+                }
+                for (int c = lane; c < C; c += 32) hv[c] = 0ull;
+            }
+            __syncthreads();
         }
-        __syncthreads();
 
         // ---- phase 5: per member v of P
         for (int32_t i = warp; i < L; i += HUB_WARPS) {
