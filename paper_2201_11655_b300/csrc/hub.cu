@@ -317,6 +317,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         }
         __syncthreads();
         const int32_t tcount = s_tcount;
+        // Q vertices per warp chunk in phases 4 and 6: 32, fewer when Q is small
+        // so that every warp gets several chunks
+        const int32_t csz = max(1, min(32, tcount / (HUB_WARPS * 4)));
         if (tcount > A.tcap) {
             if (tid == 0) s_skip = 1;
         }
@@ -401,10 +404,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 uint32_t *swq = srun + 32;
                 for (;;) {
                     int32_t c0 = 0;
-                    if (lane == 0) c0 = atomicAdd(&s_chunk4, 32);
+                    if (lane == 0) c0 = atomicAdd(&s_chunk4, csz);
                     c0 = __shfl_sync(0xffffffffu, c0, 0);
                     if (c0 >= tcount) break;
-                    const int32_t t = c0 + lane;
+                    const int32_t t = lane < csz ? c0 + lane : tcount;
                     int64_t be = 0;
                     int32_t len = 0, nb0 = 0;
                     if (t < tcount) {
@@ -783,10 +786,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
             uint32_t *sq = reinterpret_cast<uint32_t *>(hv);
             for (;;) {
                 int32_t c0 = 0;
-                if (lane == 0) c0 = atomicAdd(&s_chunk, 32);
+                if (lane == 0) c0 = atomicAdd(&s_chunk, csz);
                 c0 = __shfl_sync(0xffffffffu, c0, 0);
                 if (c0 >= tcount) break;
-                const int32_t t = c0 + lane;
+                const int32_t t = lane < csz ? c0 + lane : tcount;
                 uint32_t b = 0u, nzm = 0u;
                 int64_t be = 0;
                 int32_t len = 0, o0 = 0, o1 = 0;
