@@ -561,6 +561,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 // -- per H-neighbour u of v (light u: one per lane; heavy u: the
                 // whole warp shares its lists)
                 const int64_t dv = ve - vb;
+                const bool vshort = ve - vu <= 256;
                 for (int pass = 0; pass < 2; pass++) {
                     const int32_t jstart = pass == 0 ? lane : 0, jstep = pass == 0 ? 32 : 1;
                     for (int32_t j = jstart; j < dH; j += jstep) {
@@ -605,10 +606,17 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                             const uint32_t ec = __ldg(g.col + e);
                             const uint32_t c = ec >> 2;
                             if (in_P(c)) continue;
-                            const int32_t pc = __ldcg(posmap + c);
-                            if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
-                            const int64_t tc = -3 - (int64_t)pc;
-                            const uint32_t fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
+                            // h(v, c): a search of v's upper row when it is short (it
+                            // stays in L1), else the position of v in NP(c)
+                            uint32_t fvc;
+                            if (vshort) {
+                                fvc = search_row(g.col, vu, ve, c);
+                            } else {
+                                const int32_t pc = __ldcg(posmap + c);
+                                if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                                const int64_t tc = -3 - (int64_t)pc;
+                                fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
+                            }
                             if (!fvc) continue;
                             const uint32_t fuc = ec & 3u;
                             cqv0 += fvc == 1u; cqv1 += fvc == 2u; cqv2 += fvc == 3u;
@@ -662,16 +670,21 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 }
 
                 // -- Q side: lanes over c in NQ(v)
+                uint32_t hx9[9];
+#pragma unroll
+                for (int k = 0; k < 9; k++) hx9[k] = htx[(int64_t)i * 9 + k];
                 long long Z[9];
+#pragma unroll
                 for (int k = 0; k < 9; k++) Z[k] = 0;
                 for (int64_t e = vu + lane; e < ve; e += 32) {
                     const uint32_t ec = __ldg(g.col + e);
                     const uint32_t c = ec >> 2, f = ec & 3u;
+                    if (in_P(c)) continue;
                     const int32_t pc = __ldcg(posmap + c);
-                    if (pc >= 0) continue;
                     if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
                     const int64_t tc = -3 - (int64_t)pc;
                     uint32_t q[9], np[3] = {0u, 0u, 0u};
+#pragma unroll
                     for (int k = 0; k < 9; k++) {
                         q[k] = __ldcg(qcnt + tc * 9 + k);
                         np[k / 3] += q[k];
@@ -679,6 +692,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     const int32_t o0 = npoff[tc], o1 = npoff[tc + 1];
                     // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
                     uint32_t comT[9], comC[9];
+#pragma unroll
                     for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
                     if (dH > 0) {
                         if (o1 - o0 <= dH) {
@@ -689,8 +703,12 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                                 const uint32_t fvy = hlist_find(hlist, h0, h1, py);
                                 if (!fvy) continue;
                                 const uint32_t cy = __ldg(P + py) & 3u;
-                                comT[(cy - 1) * 3 + fvy - 1]++;
-                                comC[(cy - 1) * 3 + (ey & 3u) - 1]++;
+                                const uint32_t kt = (cy - 1) * 3 + fvy - 1, kc = (cy - 1) * 3 + (ey & 3u) - 1;
+#pragma unroll
+                                for (int k = 0; k < 9; k++) {
+                                    comT[k] += (uint32_t)k == kt ? 1u : 0u;
+                                    comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                }
                             }
                         } else {
                             for (int32_t j = 0; j < dH; j++) {
@@ -699,18 +717,24 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                                 const uint32_t fyc = hlist_find(nplist, o0, o1, yp);
                                 if (!fyc) continue;
                                 const uint32_t cy = __ldg(P + yp) & 3u;
-                                comT[(cy - 1) * 3 + (eyv & 3u) - 1]++;
-                                comC[(cy - 1) * 3 + fyc - 1]++;
+                                const uint32_t kt = (cy - 1) * 3 + (eyv & 3u) - 1, kc = (cy - 1) * 3 + fyc - 1;
+#pragma unroll
+                                for (int k = 0; k < 9; k++) {
+                                    comT[k] += (uint32_t)k == kt ? 1u : 0u;
+                                    comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                }
                             }
                         }
                     }
                     // S2 (x = v, c adjacent to v only): partner y by (colour, h(v,y))
+#pragma unroll
                     for (uint32_t be = 1; be <= 3; be++) {
                         uint32_t combe = 0u;
+#pragma unroll
                         for (uint32_t fy = 1; fy <= 3; fy++) {
                             const uint32_t k = (be - 1) * 3 + fy - 1;
                             combe += comT[k];
-                            const long long cnt = (long long)htx[(int64_t)i * 9 + k] - comT[k];
+                            const long long cnt = (long long)hx9[k] - comT[k];
                             const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
                             sadd(hv, cls, (unsigned long long)cnt);
                             gadd(S, c, cls, (unsigned long long)cnt, C);
@@ -725,13 +749,16 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     // S2 with c adjacent to v and to another P member y: credit of
                     // v, partners y in NP(c) by (colour, h(y,c)), counted as if v, y
                     // were not adjacent (H-adjacent pairs are corrected per H-edge)
+                    const uint32_t kself = (al - 1) * 3 + f - 1;
+#pragma unroll
                     for (int k = 0; k < 9; k++) {
-                        const uint32_t cnt = q[k] - ((uint32_t)k == (al - 1) * 3 + f - 1 ? 1u : 0u);
+                        const uint32_t cnt = q[k] - ((uint32_t)k == kself ? 1u : 0u);
                         sadd(hv, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
                     }
                     // S2 credit of v as the P member not adjacent to c (collected in Z)
-                    for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k];
-                    Z[(al - 1) * 3 + f - 1] -= 1;
+#pragma unroll
+                    for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k] - ((uint32_t)k == kself ? 1 : 0);
+#pragma unroll
                     for (uint32_t f2 = 1; f2 <= 3; f2++) {
                         // S3 credit of c: every other c2 in NQ(v) as partner
                         // (adjacent partners are corrected per triangle)
@@ -745,7 +772,12 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         sadd(rootD, cls, cnt4);
                     }
                 }
-                for (int k = 0; k < 9; k++) Z[k] = warp_sum(Z[k]);
+                long long zl = 0;  // Z[lane] for lanes 0..8
+#pragma unroll
+                for (int k = 0; k < 9; k++) {
+                    const long long zk = warp_sum(Z[k]);
+                    if (k == lane) zl = zk;
+                }
                 // S2 credit of v as the non-adjacent P member (x not in N_H[v])
                 if (lane < 9) {
                     long long wsum = 0;
@@ -753,7 +785,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         const uint32_t xp = j < 0 ? (uint32_t)i : (hlist[h0 + j] >> 2);
                         if ((__ldg(P + xp) & 3u) == (uint32_t)(lane / 3 + 1)) wsum += wx[xp * 3 + lane % 3];
                     }
-                    const long long base = (long long)Wtot[lane] - wsum - Z[lane];
+                    const long long base = (long long)Wtot[lane] - wsum - zl;
                     const uint32_t cls = lut[mask4((uint32_t)(lane / 3 + 1), al, 0u, 0u, (uint32_t)(lane % 3 + 1), 0u)];
                     sadd(hv, cls, (unsigned long long)base);
                 }
@@ -780,9 +812,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         // its lanes on consecutive entries, so long and short rows alike keep
         // the lanes busy.
         {
-            // [32][9] P-neighbour counts of the chunk's Q vertices, in the warp's
-            // histogram (k = 4 only; k = 3 credits b directly)
-            static_assert(K == 3 || 2 * C >= 32 * 9, "chunk counts must fit the warp histogram");
+            // [32][9] P-neighbour counts of the chunk's Q vertices and a queue of
+            // 32 triangle candidates, in the warp's histogram (k = 4 only; k = 3
+            // credits b directly)
+            static_assert(K == 3 || 2 * C >= 32 * 9 + 64, "chunk counts and candidate queue must fit the warp histogram");
             uint32_t *sq = reinterpret_cast<uint32_t *>(hv);
             for (;;) {
                 int32_t c0 = 0;
@@ -852,34 +885,36 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     if (lane >= o) incl += y;
                 }
                 const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                for (int32_t base = 0; base < total; base += 32) {
-                    const int32_t j = base + lane;
-                    // owner lane w: the first lane whose inclusive sum exceeds j
+                // owner lane of entry j: the first lane whose inclusive sum exceeds j
+                auto owner = [&](int32_t j) {
                     int32_t w = 0;
 #pragma unroll
                     for (int sh = 16; sh >= 1; sh >>= 1)
                         if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
-                    const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
+                    return w;
+                };
+                // entry j of the chunk (b's upper row ends at be); 0 past the end
+                auto entry = [&](int32_t j, int32_t w) {
                     const int64_t beo = __shfl_sync(0xffffffffu, be, w);
                     const int32_t io = __shfl_sync(0xffffffffu, incl, w);
-                    const uint32_t nzo = __shfl_sync(0xffffffffu, nzm, w);
-                    const int32_t oo0 = __shfl_sync(0xffffffffu, o0, w), oo1 = __shfl_sync(0xffffffffu, o1, w);
-                    if (j >= total) continue;
-                    const int64_t e = beo - (int64_t)(io - j);  // entries of b end at be
-                    const uint32_t ent = __ldg(g.col + e);
-                    const uint32_t c = ent >> 2;
-                    if (in_P(c)) continue;
-                    const uint32_t gg = ent & 3u;
-                    // S4 credit of c (b at depth 2, c at depth 3)
-#pragma unroll
-                    for (int k = 0; k < 9; k++)
-                        if ((nzo >> k) & 1u)
-                            gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], sq[w * 9 + k], C);
-                    // triangles v - b - c with c in NQ(b), b < c: enumerate the
-                    // S3 set and correct the bulk counts
-                    if (c <= bo || !claimed(c)) continue;  // counted from c, or no P neighbour
+                    return j < total ? __ldg(g.col + (beo - (int64_t)(io - j))) : 0u;
+                };
+                // triangle candidates (c in NQ(b), b < c, c claimed) wait in a
+                // queue and are resolved 32 at a time, one per lane
+                uint32_t *qc = sq + 32 * 9, *qm = qc + 32;
+                int32_t qn = 0;
+                auto drain = [&](int32_t cnt) {
+                    const bool act = lane < cnt;
+                    const uint32_t c = act ? qc[lane] : 0u, m = act ? qm[lane] : 0u;
+                    const int32_t wv = (int32_t)(m & 31u);
+                    const uint32_t gg = m >> 5;
+                    const uint32_t bo = __shfl_sync(0xffffffffu, b, wv);
+                    const int32_t oo0 = __shfl_sync(0xffffffffu, o0, wv), oo1 = __shfl_sync(0xffffffffu, o1, wv);
+                    __syncwarp();
+                    if (!act) return;
+                    // triangles v - b - c: enumerate the S3 set and correct the bulk counts
                     const int32_t pc = __ldcg(posmap + c);
-                    if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                    if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) return;
                     const int64_t t2 = -3 - (int64_t)pc;
                     const int32_t p0 = npoff[t2], p1 = npoff[t2 + 1];
                     const bool short_b = (oo1 - oo0) <= (p1 - p0);
@@ -899,18 +934,55 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         const uint32_t clB = lut[mask4(cv, 0u, 0u, fvc, 0u, swapf(gg))];
                         const uint32_t who[3] = {vv, bo, c};
 #pragma unroll
-                        for (int m = 0; m < 3; m++) {
-                            gadd(S, who[m], clE, 1ull, C);
-                            gadd(S, who[m], clF, ~0ull, C);
-                            gadd(S, who[m], clA, ~0ull, C);
-                            gadd(S, who[m], clB, ~0ull, C);
+                        for (int m3 = 0; m3 < 3; m3++) {
+                            gadd(S, who[m3], clE, 1ull, C);
+                            gadd(S, who[m3], clF, ~0ull, C);
+                            gadd(S, who[m3], clA, ~0ull, C);
+                            gadd(S, who[m3], clB, ~0ull, C);
                         }
                         sadd(rootD, clE, 1ull);
                         sadd(rootD, clF, ~0ull);
                         sadd(rootD, clA, ~0ull);
                         sadd(rootD, clB, ~0ull);
                     }
+                };
+                // the next window's entry is loaded before this one is processed
+                int32_t wn = owner(lane);
+                uint32_t entn = entry(lane, wn);
+                for (int32_t base = 0; base < total; base += 32) {
+                    const int32_t j = base + lane;
+                    const int32_t w = wn;
+                    const uint32_t ent = entn;
+                    wn = owner(j + 32);
+                    entn = entry(j + 32, wn);
+                    const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
+                    const uint32_t nzo = __shfl_sync(0xffffffffu, nzm, w);
+                    const uint32_t c = ent >> 2, gg = ent & 3u;
+                    bool cand = false;
+                    if (j < total && !in_P(c)) {
+                        // S4 credit of c (b at depth 2, c at depth 3)
+#pragma unroll
+                        for (int k = 0; k < 9; k++)
+                            if ((nzo >> k) & 1u)
+                                gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], sq[w * 9 + k], C);
+                        cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                    const int32_t nc = __popc(bal);
+                    if (qn + nc > 32) {
+                        drain(qn);
+                        __syncwarp();
+                        qn = 0;
+                    }
+                    if (cand) {
+                        const int32_t pos = qn + __popc(bal & lt);
+                        qc[pos] = c;
+                        qm[pos] = (uint32_t)w | (gg << 5);
+                    }
+                    qn += nc;
+                    __syncwarp();
                 }
+                if (qn > 0) drain(qn);
                 __syncwarp();
             }
             __syncwarp();
