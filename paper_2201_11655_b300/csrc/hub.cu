@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     __shared__ unsigned long long rootP[C], rootD[C];
     __shared__ unsigned long long whist[HUB_WARPS][C];
     __shared__ uint32_t esub[HUB_WARPS][27], eins[HUB_WARPS][27];
+    __shared__ uint32_t vq[HUB_WARPS][32];  // queued Q entries of a P member's row
     __shared__ unsigned long long Etype[27];
     __shared__ unsigned long long Wtot[9];
     __shared__ uint32_t ncol[3];
@@ -420,24 +421,37 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     srun[lane] = 0u;
                     swq[lane * 3 + 0] = swq[lane * 3 + 1] = swq[lane * 3 + 2] = 0u;
                     int32_t incl = len;
-    #pragma unroll
+#pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                         if (lane >= o) incl += y;
                     }
                     const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
                     __syncwarp();
-                    for (int32_t base = 0; base < total; base += 32) {
-                        const int32_t j = base + lane;
+                    // owner lane of entry j: the first lane whose inclusive sum exceeds j
+                    auto owner = [&](int32_t j) {
                         int32_t w = 0;
-    #pragma unroll
+#pragma unroll
                         for (int sh = 16; sh >= 1; sh >>= 1)
                             if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                        return w;
+                    };
+                    auto entry = [&](int32_t j, int32_t w) {
                         const int64_t beo = __shfl_sync(0xffffffffu, be, w);
                         const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                        return j < total ? __ldg(g.col + (beo - (int64_t)(io - j))) : 0u;
+                    };
+                    // the next window's entry is loaded before this one is processed
+                    int32_t wn = owner(lane);
+                    uint32_t entn = entry(lane, wn);
+                    for (int32_t base = 0; base < total; base += 32) {
+                        const int32_t j = base + lane;
+                        const int32_t w = wn;
+                        const uint32_t ent = entn;
+                        wn = owner(j + 32);
+                        entn = entry(j + 32, wn);
                         const int32_t nbo = __shfl_sync(0xffffffffu, nb0, w);
                         const bool valid = j < total;
-                        const uint32_t ent = valid ? __ldg(g.col + (beo - (int64_t)(io - j))) : 0u;
                         const bool isP = valid && in_P(ent >> 2);
                         // lanes of the same Q vertex in this window (idle lanes apart)
                         const uint32_t grp = __match_any_sync(0xffffffffu, valid ? w : 32 + lane);
@@ -456,7 +470,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     }
                     if (t < tcount) {
                         in_bounds(g, (int32_t)srun[lane] == npoff[t + 1] - nb0);
-    #pragma unroll
+#pragma unroll
                         for (int f = 0; f < 3; f++) wq[(int64_t)t * 3 + f] = swq[lane * 3 + f];
                     }
                     __syncwarp();
@@ -676,102 +690,121 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 long long Z[9];
 #pragma unroll
                 for (int k = 0; k < 9; k++) Z[k] = 0;
-                for (int64_t e = vu + lane; e < ve; e += 32) {
-                    const uint32_t ec = __ldg(g.col + e);
-                    const uint32_t c = ec >> 2, f = ec & 3u;
-                    if (in_P(c)) continue;
-                    const int32_t pc = __ldcg(posmap + c);
-                    if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
-                    const int64_t tc = -3 - (int64_t)pc;
-                    uint32_t q[9], np[3] = {0u, 0u, 0u};
+                // Q entries of v's row wait in a queue and are processed 32 at a
+                // time, one per lane
+                uint32_t *qv = vq[warp];
+                auto qside = [&](const uint32_t ec) {
+                        const uint32_t c = ec >> 2, f = ec & 3u;
+                        const int32_t pc = __ldcg(posmap + c);
+                        if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) return;
+                        const int64_t tc = -3 - (int64_t)pc;
+                        uint32_t q[9], np[3] = {0u, 0u, 0u};
 #pragma unroll
-                    for (int k = 0; k < 9; k++) {
-                        q[k] = __ldcg(qcnt + tc * 9 + k);
-                        np[k / 3] += q[k];
-                    }
-                    const int32_t o0 = npoff[tc], o1 = npoff[tc + 1];
-                    // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
-                    uint32_t comT[9], comC[9];
+                        for (int k = 0; k < 9; k++) {
+                            q[k] = __ldcg(qcnt + tc * 9 + k);
+                            np[k / 3] += q[k];
+                        }
+                        const int32_t o0 = npoff[tc], o1 = npoff[tc + 1];
+                        // NH(v) n NP(c) by (colour, h(v,y)) and by (colour, h(y,c))
+                        uint32_t comT[9], comC[9];
 #pragma unroll
-                    for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
-                    if (dH > 0) {
-                        if (o1 - o0 <= dH) {
-                            for (int32_t x = o0; x < o1; x++) {
-                                const uint32_t ey = nplist[x];
-                                const uint32_t py = ey >> 2;
-                                if (py == (uint32_t)i) continue;
-                                const uint32_t fvy = hlist_find(hlist, h0, h1, py);
-                                if (!fvy) continue;
-                                const uint32_t cy = __ldg(P + py) & 3u;
-                                const uint32_t kt = (cy - 1) * 3 + fvy - 1, kc = (cy - 1) * 3 + (ey & 3u) - 1;
+                        for (int k = 0; k < 9; k++) comT[k] = comC[k] = 0u;
+                        if (dH > 0) {
+                            if (o1 - o0 <= dH) {
+                                for (int32_t x = o0; x < o1; x++) {
+                                    const uint32_t ey = nplist[x];
+                                    const uint32_t py = ey >> 2;
+                                    if (py == (uint32_t)i) continue;
+                                    const uint32_t fvy = hlist_find(hlist, h0, h1, py);
+                                    if (!fvy) continue;
+                                    const uint32_t cy = __ldg(P + py) & 3u;
+                                    const uint32_t kt = (cy - 1) * 3 + fvy - 1, kc = (cy - 1) * 3 + (ey & 3u) - 1;
 #pragma unroll
-                                for (int k = 0; k < 9; k++) {
-                                    comT[k] += (uint32_t)k == kt ? 1u : 0u;
-                                    comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                    for (int k = 0; k < 9; k++) {
+                                        comT[k] += (uint32_t)k == kt ? 1u : 0u;
+                                        comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                    }
                                 }
-                            }
-                        } else {
-                            for (int32_t j = 0; j < dH; j++) {
-                                const uint32_t eyv = hlist[h0 + j];
-                                const uint32_t yp = eyv >> 2;
-                                const uint32_t fyc = hlist_find(nplist, o0, o1, yp);
-                                if (!fyc) continue;
-                                const uint32_t cy = __ldg(P + yp) & 3u;
-                                const uint32_t kt = (cy - 1) * 3 + (eyv & 3u) - 1, kc = (cy - 1) * 3 + fyc - 1;
+                            } else {
+                                for (int32_t j = 0; j < dH; j++) {
+                                    const uint32_t eyv = hlist[h0 + j];
+                                    const uint32_t yp = eyv >> 2;
+                                    const uint32_t fyc = hlist_find(nplist, o0, o1, yp);
+                                    if (!fyc) continue;
+                                    const uint32_t cy = __ldg(P + yp) & 3u;
+                                    const uint32_t kt = (cy - 1) * 3 + (eyv & 3u) - 1, kc = (cy - 1) * 3 + fyc - 1;
 #pragma unroll
-                                for (int k = 0; k < 9; k++) {
-                                    comT[k] += (uint32_t)k == kt ? 1u : 0u;
-                                    comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                    for (int k = 0; k < 9; k++) {
+                                        comT[k] += (uint32_t)k == kt ? 1u : 0u;
+                                        comC[k] += (uint32_t)k == kc ? 1u : 0u;
+                                    }
                                 }
                             }
                         }
-                    }
-                    // S2 (x = v, c adjacent to v only): partner y by (colour, h(v,y))
+                        // S2 (x = v, c adjacent to v only): partner y by (colour, h(v,y))
 #pragma unroll
-                    for (uint32_t be = 1; be <= 3; be++) {
-                        uint32_t combe = 0u;
+                        for (uint32_t be = 1; be <= 3; be++) {
+                            uint32_t combe = 0u;
 #pragma unroll
-                        for (uint32_t fy = 1; fy <= 3; fy++) {
-                            const uint32_t k = (be - 1) * 3 + fy - 1;
-                            combe += comT[k];
-                            const long long cnt = (long long)hx9[k] - comT[k];
-                            const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
+                            for (uint32_t fy = 1; fy <= 3; fy++) {
+                                const uint32_t k = (be - 1) * 3 + fy - 1;
+                                combe += comT[k];
+                                const long long cnt = (long long)hx9[k] - comT[k];
+                                const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
+                                sadd(hv, cls, (unsigned long long)cnt);
+                                gadd(S, c, cls, (unsigned long long)cnt, C);
+                                sadd(rootD, cls, (unsigned long long)cnt);
+                            }
+                            const long long cnt = (long long)ncol[be - 1] - hcv[be - 1] - np[be - 1] + combe;
+                            const uint32_t cls = lut[mask4(al, be, 0u, 0u, f, 0u)];
                             sadd(hv, cls, (unsigned long long)cnt);
                             gadd(S, c, cls, (unsigned long long)cnt, C);
                             sadd(rootD, cls, (unsigned long long)cnt);
                         }
-                        const long long cnt = (long long)ncol[be - 1] - hcv[be - 1] - np[be - 1] + combe;
-                        const uint32_t cls = lut[mask4(al, be, 0u, 0u, f, 0u)];
-                        sadd(hv, cls, (unsigned long long)cnt);
-                        gadd(S, c, cls, (unsigned long long)cnt, C);
-                        sadd(rootD, cls, (unsigned long long)cnt);
-                    }
-                    // S2 with c adjacent to v and to another P member y: credit of
-                    // v, partners y in NP(c) by (colour, h(y,c)), counted as if v, y
-                    // were not adjacent (H-adjacent pairs are corrected per H-edge)
-                    const uint32_t kself = (al - 1) * 3 + f - 1;
+                        // S2 with c adjacent to v and to another P member y: credit of
+                        // v, partners y in NP(c) by (colour, h(y,c)), counted as if v, y
+                        // were not adjacent (H-adjacent pairs are corrected per H-edge)
+                        const uint32_t kself = (al - 1) * 3 + f - 1;
 #pragma unroll
-                    for (int k = 0; k < 9; k++) {
-                        const uint32_t cnt = q[k] - ((uint32_t)k == kself ? 1u : 0u);
-                        sadd(hv, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
-                    }
-                    // S2 credit of v as the P member not adjacent to c (collected in Z)
+                        for (int k = 0; k < 9; k++) {
+                            const uint32_t cnt = q[k] - ((uint32_t)k == kself ? 1u : 0u);
+                            sadd(hv, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
+                        }
+                        // S2 credit of v as the P member not adjacent to c (collected in Z)
 #pragma unroll
-                    for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k] - ((uint32_t)k == kself ? 1 : 0);
+                        for (int k = 0; k < 9; k++) Z[k] += (long long)q[k] - comC[k] - ((uint32_t)k == kself ? 1 : 0);
 #pragma unroll
-                    for (uint32_t f2 = 1; f2 <= 3; f2++) {
-                        // S3 credit of c: every other c2 in NQ(v) as partner
-                        // (adjacent partners are corrected per triangle)
-                        const long long cnt3 = (long long)Wv[f2 - 1] - (f == f2);
-                        gadd(S, c, lut[mask4(al, 0u, 0u, f, f2, 0u)], (unsigned long long)cnt3, C);
-                        // S4 with (x, b) = (v, c): every Q-neighbour of c as the
-                        // depth-3 vertex (those adjacent to v corrected per triangle)
-                        const unsigned long long cnt4 = wq[tc * 3 + f2 - 1];
-                        const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
-                        sadd(hv, cls, cnt4);
-                        sadd(rootD, cls, cnt4);
+                        for (uint32_t f2 = 1; f2 <= 3; f2++) {
+                            // S3 credit of c: every other c2 in NQ(v) as partner
+                            // (adjacent partners are corrected per triangle)
+                            const long long cnt3 = (long long)Wv[f2 - 1] - (f == f2);
+                            gadd(S, c, lut[mask4(al, 0u, 0u, f, f2, 0u)], (unsigned long long)cnt3, C);
+                            // S4 with (x, b) = (v, c): every Q-neighbour of c as the
+                            // depth-3 vertex (those adjacent to v corrected per triangle)
+                            const unsigned long long cnt4 = wq[tc * 3 + f2 - 1];
+                            const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
+                            sadd(hv, cls, cnt4);
+                            sadd(rootD, cls, cnt4);
+                        }
+                };
+                int32_t qn = 0;
+                for (int64_t e0 = vu; e0 < ve; e0 += 32) {
+                    const int64_t e = e0 + lane;
+                    const uint32_t ent = e < ve ? __ldg(g.col + e) : 0u;
+                    const bool isQ = e < ve && !in_P(ent >> 2);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, isQ);
+                    const int32_t nc = __popc(bal);
+                    if (qn + nc > 32) {
+                        if (lane < qn) qside(qv[lane]);
+                        __syncwarp();
+                        qn = 0;
                     }
+                    if (isQ) qv[qn + __popc(bal & lt)] = ent;
+                    qn += nc;
+                    __syncwarp();
                 }
+                if (lane < qn) qside(qv[lane]);
+                __syncwarp();
                 long long zl = 0;  // Z[lane] for lanes 0..8
 #pragma unroll
                 for (int k = 0; k < 9; k++) {
