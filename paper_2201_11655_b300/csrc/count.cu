@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     uint8_t *lut = (uint8_t *)(smem + (size_t)nwarps * NH * C);
-    unsigned long long *hist_r = smem + (size_t)warp * NH * C;
-    unsigned long long *hist_a = hist_r + C;
-    unsigned long long *hist_b = hist_r + 2 * C;  // K == 4 only
+    const Hist64 hist_r = hist64(smem + (size_t)warp * NH * C, C);
+    const Hist64 hist_a = hist64(smem + (size_t)warp * NH * C + C, C);
+    const Hist64 hist_b = hist64(smem + (size_t)warp * NH * C + 2 * C, C);  // K == 4 only
     // A disconnected index never reaches the table by construction; should
     // one appear, it is counted in no column and flags the status word.
     for (int i = threadIdx.x; i < NIDX; i += blockDim.x) {
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                     const uint32_t b = eb >> 2, frb = eb & 3u;
                     const uint32_t cls = lut[mask3(fra, frb, pair_flags(g, a, b))];
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                    atomicAdd(&hist_r[cls], 1ull);
-                    atomicAdd(&hist_a[cls], 1ull);
+                    hinc(hist_r, cls);
+                    hinc(hist_a, cls);
                     credit(g, out, G.new2old, b, C, cls);
                 }
                 // path: b in N(a) \ N(r), b > r
@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                     if (search_row(g.col, pb, pe, b)) continue;
                     const uint32_t cls = lut[mask3(fra, 0u, eb & 3u)];
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                    atomicAdd(&hist_r[cls], 1ull);
-                    atomicAdd(&hist_a[cls], 1ull);
+                    hinc(hist_r, cls);
+                    hinc(hist_a, cls);
                     credit(g, out, G.new2old, b, C, cls);
                 }
             } else {
@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         const uint32_t c = ec >> 2, frc = ec & 3u;
                         const uint32_t cls = lut[mask4(fra, frb, frc, fab, pair_flags(g, a, c), pair_flags(g, b, c))];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        atomicAdd(&hist_r[cls], 1ull);
-                        atomicAdd(&hist_a[cls], 1ull);
-                        atomicAdd(&hist_b[cls], 1ull);
+                        hinc(hist_r, cls);
+                        hinc(hist_a, cls);
+                        hinc(hist_b, cls);
                         credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,1,2) with c in N(a) \ N(r), c > r
@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (search_row(g.col, pb, pe, c)) continue;
                         const uint32_t cls = lut[mask4(fra, frb, 0u, fab, ec & 3u, pair_flags(g, b, c))];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        atomicAdd(&hist_r[cls], 1ull);
-                        atomicAdd(&hist_a[cls], 1ull);
-                        atomicAdd(&hist_b[cls], 1ull);
+                        hinc(hist_r, cls);
+                        hinc(hist_a, cls);
+                        hinc(hist_b, cls);
                         credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,1,2) with c in N(b) \ N(a) \ N(r), c > r
@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (pair_flags(g, a, c)) continue;
                         const uint32_t cls = lut[mask4(fra, frb, 0u, fab, 0u, ec & 3u)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        atomicAdd(&hist_r[cls], 1ull);
-                        atomicAdd(&hist_a[cls], 1ull);
-                        atomicAdd(&hist_b[cls], 1ull);
+                        hinc(hist_r, cls);
+                        hinc(hist_a, cls);
+                        hinc(hist_b, cls);
                         credit(g, out, G.new2old, c, C, cls);
                     }
                     flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
@@ -232,9 +232,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (search_row(g.col, pb, pe, c)) continue;
                         const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, ec & 3u, pair_flags(g, b, c))];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        atomicAdd(&hist_r[cls], 1ull);
-                        atomicAdd(&hist_a[cls], 1ull);
-                        atomicAdd(&hist_b[cls], 1ull);
+                        hinc(hist_r, cls);
+                        hinc(hist_a, cls);
+                        hinc(hist_b, cls);
                         credit(g, out, G.new2old, c, C, cls);
                     }
                     // (1,2,3): c in N(b), c > r, not in N(r), not adjacent to a
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
                         if (pair_flags(g, a, c)) continue;
                         const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, 0u, ec & 3u)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        atomicAdd(&hist_r[cls], 1ull);
-                        atomicAdd(&hist_a[cls], 1ull);
-                        atomicAdd(&hist_b[cls], 1ull);
+                        hinc(hist_r, cls);
+                        hinc(hist_a, cls);
+                        hinc(hist_b, cls);
                         credit(g, out, G.new2old, c, C, cls);
                     }
                     flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);

@@ -112,19 +112,50 @@ __device__ __forceinline__ void credit(const Csr &g, uint64_t *out, const int32_
     atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], 1ull);
 }
 
-__device__ __forceinline__ void flush_hist(const Csr &g, unsigned long long *hist, int C, uint64_t *out,
-                                           int32_t orig, int lane) {
-    __syncwarp();
-    if (!in_bounds(g, orig >= 0 && orig < g.n)) {
-        for (int c = lane; c < C; c += 32) hist[c] = 0ull;
-        __syncwarp();
-        return;
+// A uint64 histogram in shared memory kept as 32-bit halves (lo[C], hi[C])
+// in the same C * 8 bytes.  An add is one native 32-bit shared atomic on the
+// low half, plus one on the high half only for the carry of a wrap (or the
+// upper word of a large or negative add); 64-bit shared-memory atomics are
+// compare-and-swap loops that collapse when many lanes hit one counter.
+// Exact modulo 2^64 once all adds have completed.
+struct Hist64 {
+    uint32_t *lo, *hi;
+};
+
+__device__ __forceinline__ Hist64 hist64(unsigned long long *h, int C) {
+    return Hist64{reinterpret_cast<uint32_t *>(h), reinterpret_cast<uint32_t *>(h) + C};
+}
+
+__device__ __forceinline__ void hadd(const Hist64 &h, uint32_t i, unsigned long long v) {
+    const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
+    uint32_t carry = 0u;
+    if (vl) {
+        const uint32_t old = atomicAdd(h.lo + i, vl);
+        carry = (uint32_t)(old + vl) < old ? 1u : 0u;
     }
+    if (vh + carry) atomicAdd(h.hi + i, vh + carry);
+}
+
+__device__ __forceinline__ void hinc(const Hist64 &h, uint32_t i) {
+    if (atomicAdd(h.lo + i, 1u) == 0xffffffffu) atomicAdd(h.hi + i, 1u);
+}
+
+__device__ __forceinline__ unsigned long long hget(const Hist64 &h, uint32_t i) {
+    return ((unsigned long long)h.hi[i] << 32) | h.lo[i];
+}
+
+// add a warp's histogram to output row orig (one global atomic per non-zero
+// column) and leave it zero
+__device__ __forceinline__ void flush_hist(const Csr &g, const Hist64 &h, int C, uint64_t *out, int32_t orig,
+                                           int lane) {
+    __syncwarp();
+    const bool ok = in_bounds(g, orig >= 0 && orig < g.n);
     for (int c = lane; c < C; c += 32) {
-        unsigned long long v = hist[c];
+        const unsigned long long v = hget(h, c);
         if (v) {
-            atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
-            hist[c] = 0ull;
+            if (ok) atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
+            h.lo[c] = 0u;
+            h.hi[c] = 0u;
         }
     }
     __syncwarp();

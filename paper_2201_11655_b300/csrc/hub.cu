@@ -125,8 +125,8 @@ __device__ __forceinline__ void gadd(const Sink &A, uint32_t v, uint32_t cls, un
     atomicAdd((unsigned long long *)&A.out[(int64_t)o * C + cls], cnt);
 }
 
-__device__ __forceinline__ void sadd(unsigned long long *h, uint32_t cls, unsigned long long cnt) {
-    if (cnt) atomicAdd(&h[cls], cnt);
+__device__ __forceinline__ void sadd(const Hist64 &h, uint32_t cls, unsigned long long cnt) {
+    if (cnt) hadd(h, cls, cnt);
 }
 
 // exclusive scan of hptr[0, L) in place (hptr[L] = total), whole CTA
@@ -229,6 +229,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     auto claimed = [&](uint32_t u) -> bool { return ((__ldcg(tbits + (u >> 5)) >> (u & 31u)) & 1u) != 0u; };
     uint32_t *nplist = A.nplist + slot * A.npcap;
     unsigned long long *hv = whist[warp];
+    const Hist64 hvh = hist64(hv, C), hP = hist64(rootP, C), hD = hist64(rootD, C);
+    const Hist64 hE = hist64(Etype, 27), hW = hist64(Wtot, 9);
 
     for (int i = tid; i < NIDX; i += HUB_THREADS) lut[i] = A.lut_g[i];
     for (int i = tid; i < A.pbits_words; i += HUB_THREADS) pbits[i] = 0u;
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         const uint32_t k9 = (cu - 1) * 3 + (f - 1);
                         t0 += k9 == 0; t1 += k9 == 1; t2 += k9 == 2; t3 += k9 == 3; t4 += k9 == 4;
                         t5 += k9 == 5; t6 += k9 == 6; t7 += k9 == 7; t8 += k9 == 8;
-                        if (i < p) atomicAdd(&Etype[etype(fx, cu, f)], 1ull);
+                        if (i < p) hinc(hE, (uint32_t)etype(fx, cu, f));
                     } else if (valid && p <= -3) {
                         const int64_t t = -3 - (int64_t)p;
                         atomicAdd(qcnt + t * 9 + (fx - 1) * 3 + (f - 1), 1u);
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
                     for (int f = 0; f < 3; f++) {
                         const uint32_t w = wx[i * 3 + f];
-                        if (w) atomicAdd(&Wtot[(fx - 1) * 3 + f], (unsigned long long)w);
+                        if (w) hadd(hW, (uint32_t)((fx - 1) * 3 + f), (unsigned long long)w);
                     }
                 }
             }
@@ -500,19 +502,19 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     const uint32_t be = lane + 1;
                     const long long cnt = (long long)ncol[lane] - (al == be) - hcv[lane];
                     const uint32_t cls = lut[mask3(al, be, 0u)];
-                    sadd(hv, cls, (unsigned long long)cnt);
-                    sadd(rootP, cls, (unsigned long long)cnt);
+                    sadd(hvh, cls, (unsigned long long)cnt);
+                    sadd(hP, cls, (unsigned long long)cnt);
                     // path with v as the depth-1 vertex: by flag
                     const uint32_t cls2 = lut[mask3(al, 0u, be)];
-                    sadd(hv, cls2, Wv[lane]);
-                    sadd(rootD, cls2, Wv[lane]);
+                    sadd(hvh, cls2, Wv[lane]);
+                    sadd(hD, cls2, Wv[lane]);
                 }
                 for (int32_t j = lane; j < dH; j += 32) {
                     const uint32_t eu = hlist[h0 + j];
                     const uint32_t cu = __ldg(P + (eu >> 2)) & 3u;
                     const uint32_t cls = lut[mask3(al, cu, eu & 3u)];
-                    sadd(hv, cls, 1ull);
-                    sadd(rootP, cls, 1ull);
+                    sadd(hvh, cls, 1ull);
+                    sadd(hP, cls, 1ull);
                 }
             } else {
                 // -- S1 per-member counts: H-edges inside R_v = P \ N_H[v] by type
@@ -549,14 +551,14 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 __syncwarp();
                 // e_tau(R_v) = E_tau - (edges touching N_H[v])
                 for (int k = lane; k < 27; k += 32) {
-                    const long long e = (long long)Etype[k] - esub[warp][k] + eins[warp][k];
+                    const long long e = (long long)hget(hE, k) - esub[warp][k] + eins[warp][k];
                     esub[warp][k] = (uint32_t)e;
                     const uint32_t be = k / 9 + 1, ga = (k / 3) % 3 + 1, f = k % 3 + 1;
                     if (e > 0) {
                         // S1 one H-edge (y,z) of type k, v isolated from both
                         const uint32_t cls = lut[mask4(be, ga, al, f, 0u, 0u)];
-                        sadd(hv, cls, (unsigned long long)e);
-                        sadd(rootP, cls, (unsigned long long)e);
+                        sadd(hvh, cls, (unsigned long long)e);
+                        sadd(hP, cls, (unsigned long long)e);
                     }
                 }
                 __syncwarp();
@@ -569,8 +571,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     long long pairs = be < ga ? ab * ag : ab * (ab - 1) / 2;
                     for (uint32_t f = 1; f <= 3; f++) pairs -= (long long)esub[warp][(be - 1) * 9 + (ga - 1) * 3 + (f - 1)];
                     const uint32_t cls = lut[mask4(al, be, ga, 0u, 0u, 0u)];
-                    sadd(hv, cls, (unsigned long long)pairs);
-                    sadd(rootP, cls, (unsigned long long)pairs);
+                    sadd(hvh, cls, (unsigned long long)pairs);
+                    sadd(hP, cls, (unsigned long long)pairs);
                 }
                 // -- per H-neighbour u of v (light u: one per lane; heavy u: the
                 // whole warp shares its lists)
@@ -606,8 +608,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                             for (uint32_t ga = 1; ga <= 3; ga++) {
                                 const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - hcx[up * 3 + ga - 1] + com[ga - 1];
                                 const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
-                                sadd(hv, cls, (unsigned long long)cnt);
-                                sadd(rootP, cls, (unsigned long long)cnt);
+                                sadd(hvh, cls, (unsigned long long)cnt);
+                                sadd(hP, cls, (unsigned long long)cnt);
                             }
                         }
                         // S2 across the H-edge (v,u), handled once by the endpoint of
@@ -639,14 +641,14 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                             // the pair out of c's non-adjacent-pair count
                             const uint32_t cle = lut[mask4(al, cu, 0u, fvu, fvc, fuc)];
                             const uint32_t clb = lut[mask4(al, cu, 0u, 0u, fvc, fuc)];
-                            sadd(hv, cle, 1ull);
+                            sadd(hvh, cle, 1ull);
                             gadd(S, u, cle, 1ull, C);
                             gadd(S, c, cle, 1ull, C);
-                            sadd(rootD, cle, 1ull);
-                            sadd(hv, clb, ~0ull);
+                            sadd(hD, cle, 1ull);
+                            sadd(hvh, clb, ~0ull);
                             gadd(S, u, clb, ~0ull, C);
                             gadd(S, c, clb, ~0ull, C);
-                            sadd(rootD, clb, ~0ull);
+                            sadd(hD, clb, ~0ull);
                         }
                         if (coop) {
                             cqv0 = warp_sum(cqv0); cqv1 = warp_sum(cqv1); cqv2 = warp_sum(cqv2);
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         if (!coop || lane == 0) {
                             for (uint32_t f = 1; f <= 3; f++) {
                                 gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)(Wv[f - 1] - cqv[f - 1]), C);
-                                sadd(hv, lut[mask4(cu, al, 0u, fuv, f, 0u)], (unsigned long long)(wx[up * 3 + f - 1] - cqu[f - 1]));
+                                sadd(hvh, lut[mask4(cu, al, 0u, fuv, f, 0u)], (unsigned long long)(wx[up * 3 + f - 1] - cqu[f - 1]));
                             }
                         }
                     }
@@ -675,10 +677,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         const uint32_t fyz = hlist_find(hlist, y0, y1, zp);
                         if (fyz == 0u || (uint32_t)i < yp) {
                             const uint32_t cls = lut[mask4(al, cy, cz, fvy, fvz, fyz)];
-                            sadd(hv, cls, 1ull);
+                            sadd(hvh, cls, 1ull);
                             gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
                             gadd(S, __ldg(P + zp) >> 2, cls, 1ull, C);
-                            sadd(rootP, cls, 3ull);
+                            sadd(hP, cls, 3ull);
                         }
                     }
                 }
@@ -751,15 +753,15 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                                 combe += comT[k];
                                 const long long cnt = (long long)hx9[k] - comT[k];
                                 const uint32_t cls = lut[mask4(al, be, 0u, fy, f, 0u)];
-                                sadd(hv, cls, (unsigned long long)cnt);
+                                sadd(hvh, cls, (unsigned long long)cnt);
                                 gadd(S, c, cls, (unsigned long long)cnt, C);
-                                sadd(rootD, cls, (unsigned long long)cnt);
+                                sadd(hD, cls, (unsigned long long)cnt);
                             }
                             const long long cnt = (long long)ncol[be - 1] - hcv[be - 1] - np[be - 1] + combe;
                             const uint32_t cls = lut[mask4(al, be, 0u, 0u, f, 0u)];
-                            sadd(hv, cls, (unsigned long long)cnt);
+                            sadd(hvh, cls, (unsigned long long)cnt);
                             gadd(S, c, cls, (unsigned long long)cnt, C);
-                            sadd(rootD, cls, (unsigned long long)cnt);
+                            sadd(hD, cls, (unsigned long long)cnt);
                         }
                         // S2 with c adjacent to v and to another P member y: credit of
                         // v, partners y in NP(c) by (colour, h(y,c)), counted as if v, y
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
 #pragma unroll
                         for (int k = 0; k < 9; k++) {
                             const uint32_t cnt = q[k] - ((uint32_t)k == kself ? 1u : 0u);
-                            sadd(hv, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
+                            sadd(hvh, lut[mask4(al, (uint32_t)(k / 3 + 1), 0u, 0u, f, (uint32_t)(k % 3 + 1))], cnt);
                         }
                         // S2 credit of v as the P member not adjacent to c (collected in Z)
 #pragma unroll
@@ -783,8 +785,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                             // depth-3 vertex (those adjacent to v corrected per triangle)
                             const unsigned long long cnt4 = wq[tc * 3 + f2 - 1];
                             const uint32_t cls = lut[mask4(al, 0u, 0u, f, 0u, f2)];
-                            sadd(hv, cls, cnt4);
-                            sadd(rootD, cls, cnt4);
+                            sadd(hvh, cls, cnt4);
+                            sadd(hD, cls, cnt4);
                         }
                 };
                 int32_t qn = 0;
@@ -818,9 +820,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                         const uint32_t xp = j < 0 ? (uint32_t)i : (hlist[h0 + j] >> 2);
                         if ((__ldg(P + xp) & 3u) == (uint32_t)(lane / 3 + 1)) wsum += wx[xp * 3 + lane % 3];
                     }
-                    const long long base = (long long)Wtot[lane] - wsum - zl;
+                    const long long base = (long long)hget(hW, lane) - wsum - zl;
                     const uint32_t cls = lut[mask4((uint32_t)(lane / 3 + 1), al, 0u, 0u, (uint32_t)(lane % 3 + 1), 0u)];
-                    sadd(hv, cls, (unsigned long long)base);
+                    sadd(hvh, cls, (unsigned long long)base);
                 }
                 // S3 credit of v and r: pairs {b, c} c NQ(v) by flags (adjacent
                 // pairs corrected per triangle)
@@ -830,12 +832,12 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     const long long pairs = f1 < f2 ? (long long)Wv[f1 - 1] * Wv[f2 - 1]
                                                     : (long long)Wv[f1 - 1] * ((long long)Wv[f1 - 1] - 1) / 2;
                     const uint32_t cls = lut[mask4(al, 0u, 0u, f1, f2, 0u)];
-                    sadd(hv, cls, (unsigned long long)pairs);
-                    sadd(rootD, cls, (unsigned long long)pairs);
+                    sadd(hvh, cls, (unsigned long long)pairs);
+                    sadd(hD, cls, (unsigned long long)pairs);
                 }
             }
             __syncwarp();
-            flush_hist(g, hv, C, A.out, row_of(A.new2old, v), lane);
+            flush_hist(g, hvh, C, A.out, row_of(A.new2old, v), lane);
         }
         __syncthreads();
 
@@ -897,14 +899,14 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                                 const unsigned long long cnt = q1 * (q1 - 1ull) / 2ull;
                                 const uint32_t cls = lut[mask4(c1, c1, 0u, 0u, h1, h1)];
                                 gadd(S, b, cls, cnt, C);
-                                sadd(rootD, cls, cnt);
+                                sadd(hD, cls, cnt);
                             }
                             for (uint32_t m2 = m1 & (m1 - 1u); m2; m2 &= m2 - 1u) {
                                 const int t2 = __ffs(m2) - 1;
                                 const unsigned long long cnt = q1 * sq[lane * 9 + t2];
                                 const uint32_t cls = lut[mask4(c1, (uint32_t)(t2 / 3 + 1), 0u, 0u, h1, (uint32_t)(t2 % 3 + 1))];
                                 gadd(S, b, cls, cnt, C);
-                                sadd(rootD, cls, cnt);
+                                sadd(hD, cls, cnt);
                             }
                         }
                     }
@@ -973,10 +975,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                             gadd(S, who[m3], clA, ~0ull, C);
                             gadd(S, who[m3], clB, ~0ull, C);
                         }
-                        sadd(rootD, clE, 1ull);
-                        sadd(rootD, clF, ~0ull);
-                        sadd(rootD, clA, ~0ull);
-                        sadd(rootD, clB, ~0ull);
+                        sadd(hD, clE, 1ull);
+                        sadd(hD, clF, ~0ull);
+                        sadd(hD, clA, ~0ull);
+                        sadd(hD, clB, ~0ull);
                     }
                 };
                 // the next window's entry is loaded before this one is processed
@@ -1027,7 +1029,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         {
             const int32_t orig = row_of(A.new2old, (uint32_t)r);
             for (int c = tid; c < C; c += HUB_THREADS) {
-                const unsigned long long v = rootP[c] / (K == 3 ? 2ull : 3ull) + rootD[c];
+                const unsigned long long v = hget(hP, c) / (K == 3 ? 2ull : 3ull) + hget(hD, c);
                 if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
             }
         }
