@@ -124,6 +124,7 @@ void free_union(vdmc_graph *U) {
     cudaFree(U->qhead);
     cudaFree(U->status);
     cudaFree(U->racc);
+    cudaFree(U->d3acc);
     vdmc_hub_free(U);
     if (U->side) cudaStreamDestroy(U->side);
     if (U->ev_fork) cudaEventDestroy(U->ev_fork);

@@ -260,15 +260,32 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
     }
 }
 
-// out[new2old[r]] = acc[r], one warp per row (coalesced row copies)
-__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const int32_t *__restrict__ new2old, int32_t n,
+// out[new2old[r]] = acc[r] (+ the depth-3 credits d3[r], k = 4), one warp
+// per row (coalesced row copies).  Column j = 3 * type + flag - 1 of d3
+// holds sets r' - x - b - c credited to c: type = (colour of x, h(x, b)),
+// flag = h(b, c); its class is that of mask4(colour, 0, 0, h(x,b), 0, h(b,c)).
+__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ d3,
+                               const uint8_t *__restrict__ lut, const int32_t *__restrict__ new2old, int32_t n,
                                int C, uint64_t *__restrict__ out) {
+    __shared__ uint8_t d3cls[27];
+    if (d3 && threadIdx.x < 27) {
+        const uint32_t j = threadIdx.x, k = j / 3;
+        d3cls[j] = lut[mask4(k / 3 + 1, 0u, 0u, k % 3 + 1, 0u, j % 3 + 1)];
+    }
+    __syncthreads();
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const int32_t o = __ldg(new2old + r);
     if (o < 0 || o >= n) return;
-    for (int c = lane; c < C; c += 32) out[(int64_t)o * C + c] = acc[r * C + c];
+    for (int c = lane; c < C; c += 32) {
+        uint64_t v = acc[r * C + c];
+        if (d3) {
+            for (int j = 0; j < 27; j++)
+                if (d3cls[j] == c) v += d3[r * 27 + j];
+        }
+        out[(int64_t)o * C + c] = v;
+    }
 }
 
 // Algorithmic bytes of one count: the adjacency rows each method must read
@@ -400,15 +417,26 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     }
     uint64_t *acc = g->racc;
     if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
+    // depth-3 credits of the root-per-CTA kernel (k = 4): 27 columns per
+    // vertex instead of 199, so that their reductions mostly stay in L2
+    uint64_t *d3 = nullptr;
+    if (k == 4 && g->nhubs > 0 && g->n > 0) {
+        if (!g->d3acc) {
+            VDMC_CUDA_TRY(cudaStreamSynchronize(s));
+            VDMC_CUDA_TRY(cudaMalloc((void **)&g->d3acc, sizeof(uint64_t) * (size_t)g->n * 27));
+        }
+        d3 = g->d3acc;
+        VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, sizeof(uint64_t) * (size_t)g->n * 27, s));
+    }
+    const uint8_t *lut = nullptr;
+    VDMC_CUDA_TRY(device_lut(k, &lut));
     GraphDesc d{g->rowptr, g->col, g->pbeg, nullptr, acc, g->n, 0, g->nnz};
     if (g->nhubs > 0) {
         // the root-per-CTA kernel runs on the graph's side stream, overlapped
         // with the warp kernel; the caller's stream waits for both
-        const uint8_t *lut = nullptr;
-        VDMC_CUDA_TRY(device_lut(k, &lut));
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
         VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vdmc_status st = vdmc_hub_launch(g, k, acc, lut, lo, hi, sch.hub_blocks_per_sm, g->side);
+        vdmc_status st = vdmc_hub_launch(g, k, acc, d3, lut, lo, hi, sch.hub_blocks_per_sm, g->side);
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
     }
@@ -416,7 +444,7 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     if (g->nhubs > 0) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
     if (st != VDMC_OK) return st;
     if (g->n > 0) {
-        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, g->new2old, g->n, C, out);
+        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, d3, lut, g->new2old, g->n, C, out);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     return VDMC_OK;

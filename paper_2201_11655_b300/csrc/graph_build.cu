@@ -217,6 +217,7 @@ void free_graph_buffers(vdmc_graph *g) {
     vdmc_hub_free(g);
     vdmc_batch_plan_free(g);
     cudaFree(g->racc);
+    cudaFree(g->d3acc);
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
@@ -439,6 +440,7 @@ extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *i
     info->num_hub_roots = g->nhubs;
     info->device_bytes += (int64_t)g->hub_scratch_bytes;
     if (g->racc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES);
+    if (g->d3acc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * 27);
     return VDMC_OK;
 }
 

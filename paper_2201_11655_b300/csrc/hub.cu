@@ -59,6 +59,7 @@ struct HubArgs {
     Csr g;
     const int32_t *new2old;
     uint64_t *out;
+    unsigned long long *d3;  // k = 4: n * 27 depth-3 credits (rank space)
     const uint8_t *lut_g;
     const int32_t *hubs;
     int32_t nhubs;
@@ -995,11 +996,14 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                     const uint32_t c = ent >> 2, gg = ent & 3u;
                     bool cand = false;
                     if (j < total && !in_P(c)) {
-                        // S4 credit of c (b at depth 2, c at depth 3)
+                        // S4 credit of c (b at depth 2, c at depth 3), in c's
+                        // depth-3 columns (type of x, h(b, c))
+                        if (nzo && in_bounds(g, c < (uint32_t)g.n && gg != 0u)) {
 #pragma unroll
-                        for (int k = 0; k < 9; k++)
-                            if ((nzo >> k) & 1u)
-                                gadd(S, c, lut[mask4((uint32_t)(k / 3 + 1), 0u, 0u, (uint32_t)(k % 3 + 1), 0u, gg)], sq[w * 9 + k], C);
+                            for (int k = 0; k < 9; k++)
+                                if ((nzo >> k) & 1u)
+                                    atomicAdd(A.d3 + (int64_t)c * 27 + k * 3 + gg - 1, (unsigned long long)sq[w * 9 + k]);
+                        }
                         cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, cand);
@@ -1176,8 +1180,8 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
 
 int vdmc_hub_count(const vdmc_graph *g) { return g->nhubs; }
 
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *lut, int32_t lo, int32_t hi,
-                            int blocks_per_sm, cudaStream_t s) {
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
+                            int32_t hi, int blocks_per_sm, cudaStream_t s) {
     if (g->nhubs <= 0) return VDMC_OK;
     int dev = 0, sms = 0;
     VDMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -1210,6 +1214,7 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *
     A.g = Csr{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
     A.new2old = nullptr;  // credits in rank space (see vdmc_count_internal)
     A.out = out;
+    A.d3 = (unsigned long long *)d3;
     A.lut_g = lut;
     A.hubs = g->hubs;
     A.nhubs = g->nhubs;

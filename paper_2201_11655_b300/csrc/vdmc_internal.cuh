@@ -62,6 +62,7 @@ struct vdmc_graph {
     int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
     uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
+    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * 27 (rank space)
 };
 
 // ---- status helpers ----
@@ -112,6 +113,6 @@ void vdmc_current_schedule(vdmc_schedule_t *s);
 
 // ---- root-per-CTA kernel (hub.cu) ----
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, const uint8_t *lut, int32_t lo, int32_t hi,
-                            int blocks_per_sm, cudaStream_t s);
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
+                            int32_t hi, int blocks_per_sm, cudaStream_t s);
 void vdmc_hub_free(vdmc_graph *g);
