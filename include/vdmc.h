@@ -80,7 +80,13 @@ typedef struct {
                                    0 = every root to the warp-per-task kernel */
     int32_t hub_blocks_per_sm;  /* root-per-CTA kernel: CTAs per SM (>= 1); each
                                    owns a scratch slot of about 4n + 52 tcap bytes */
-    int32_t reserved[3];
+    int32_t hub_split;          /* root-per-CTA kernel: the largest roots are
+                                   each counted by this many CTAs (0..16; 0 or 1 =
+                                   no split); every part builds the root's lists and
+                                   takes a share of its members and second-hop
+                                   vertices */
+    int32_t hub_split_roots;    /* how many of the largest roots are split (>= 0) */
+    int32_t reserved[1];
 } vdmc_schedule_t;
 
 /*

@@ -11,10 +11,12 @@ tests):
                      (work-queue granularity)
   warps_per_block    warps per CTA of the warp-per-task kernel (its shared
                      memory -- per-warp credit histograms -- grows with it)
+  hub_split,         the largest hub_split_roots roots are each counted by
+  hub_split_roots    hub_split CTAs (the critical path of fat-tailed graphs)
 
 The search is staged: the two root-per-CTA knobs first (they dominate on
 fat-tailed graphs), then the two warp-kernel knobs with the best of the
-first stage.  Each candidate is timed with CUDA events after a warm-up
+first stage, then the root split.  Each candidate is timed with CUDA events after a warm-up
 count.  Results are stored per (k, size bucket) in ``tuned_schedules.json``
 next to this file; ``apply_tuned`` loads the entry for a graph's bucket.
 
@@ -35,6 +37,8 @@ TUNED_PATH = os.path.join(HERE, "tuned_schedules.json")
 STAGE1 = ([{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024) for b in (1, 2)] +
           [{"hub_min_l": 0, "hub_blocks_per_sm": 1}])
 STAGE2 = [{"a_chunk": a, "warps_per_block": w} for a in (4, 16, 64) for w in (4, 8)]
+STAGE3 = ([{"hub_split": 1, "hub_split_roots": 0}] +
+          [{"hub_split": s, "hub_split_roots": r} for s, r in ((2, 32), (2, 64), (2, 128), (4, 16), (4, 48), (8, 12))])
 
 
 def bucket(n: int, m: int) -> str:
@@ -60,30 +64,23 @@ def time_count(g, k, reps=1):
     return best
 
 
-def tune(g, k, stage1=STAGE1, stage2=STAGE2, reps=1, log=print):
+def tune(g, k, stage1=STAGE1, stage2=STAGE2, stage3=STAGE3, reps=1, log=print):
     """Staged search on graph g; returns (best schedule dict, {str(candidate): ms})."""
     from . import vdmc
     base = vdmc.get_schedule()
     timings = {}
     best, best_ms = dict(base), float("inf")
     try:
-        for cand in stage1:
-            sch = dict(base, **cand)
-            vdmc.set_schedule(**sch)
-            ms = time_count(g, k, reps)
-            timings[json.dumps(cand, sort_keys=True)] = ms
-            log("stage1 %s: %.2f ms" % (cand, ms))
-            if ms < best_ms:
-                best, best_ms = sch, ms
-        base2 = dict(best)
-        for cand in stage2:
-            sch = dict(base2, **cand)
-            vdmc.set_schedule(**sch)
-            ms = time_count(g, k, reps)
-            timings[json.dumps(cand, sort_keys=True)] = ms
-            log("stage2 %s: %.2f ms" % (cand, ms))
-            if ms < best_ms:
-                best, best_ms = sch, ms
+        for name, stage in (("stage1", stage1), ("stage2", stage2), ("stage3", stage3)):
+            base_s = dict(best) if best_ms < float("inf") else dict(base)
+            for cand in stage:
+                sch = dict(base_s, **cand)
+                vdmc.set_schedule(**sch)
+                ms = time_count(g, k, reps)
+                timings[json.dumps(cand, sort_keys=True)] = ms
+                log("%s %s: %.2f ms" % (name, cand, ms))
+                if ms < best_ms:
+                    best, best_ms = sch, ms
     finally:
         vdmc.set_schedule(**base)
     return best, best_ms, timings
@@ -141,7 +138,8 @@ def main():
     if a.hub_min_l:
         keep = {int(x) for x in a.hub_min_l.split(",")}
         stage1 = [c for c in STAGE1 if c["hub_min_l"] in keep]
-    best, ms, timings = tune(g, a.k, stage1=stage1, stage2=[] if a.skip_stage2 else STAGE2, reps=a.reps)
+    best, ms, timings = tune(g, a.k, stage1=stage1, stage2=[] if a.skip_stage2 else STAGE2,
+                             stage3=[] if a.skip_stage2 else STAGE3, reps=a.reps)
     key = "k%d/%s" % (a.k, bucket(n, m))
     save_tuned(key, best, ms, {"workload": name, "n": n, "m": m, "timings_ms": timings,
                                "tuned_seconds": round(time.time() - t0, 1)}, a.out)

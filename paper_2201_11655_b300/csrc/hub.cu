@@ -63,6 +63,11 @@ struct HubArgs {
     const uint8_t *lut_g;
     const int32_t *hubs;
     int32_t nhubs;
+    // the first nsplit hub roots are split into `split` parts (queue entries
+    // e * split + part); the parts sum their three-member partials in
+    // split_acc[e], which split_finish divides and credits after the kernel
+    int32_t nsplit, split;
+    unsigned long long *split_acc;  // nsplit * C
     int32_t rank_lo, rank_hi;
     unsigned long long *qhead;
     // per-slot scratch
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     __shared__ unsigned long long Etype[27];
     __shared__ unsigned long long Wtot[9];
     __shared__ uint32_t ncol[3];
-    __shared__ int32_t s_root, s_tcount, s_total, s_skip, s_chunk, s_chunk4;
+    __shared__ int32_t s_root, s_part, s_esplit, s_tcount, s_total, s_skip, s_chunk, s_chunk4, s_vnext;
     __shared__ int32_t warp_sums[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -240,8 +245,19 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            unsigned long long q = atomicAdd(A.qhead, 1ull);
-            s_root = q < (unsigned long long)A.nhubs ? A.hubs[q] : -1;
+            const unsigned long long q = atomicAdd(A.qhead, 1ull);
+            const unsigned long long qs = (unsigned long long)A.nsplit * A.split;
+            if (q < qs) {
+                s_root = A.hubs[q / A.split];
+                s_part = (int32_t)(q % A.split);
+                s_esplit = (int32_t)(q / A.split);
+            } else {
+                const unsigned long long h = q - qs + A.nsplit;
+                s_root = h < (unsigned long long)A.nhubs ? A.hubs[h] : -1;
+                s_part = -1;
+                s_esplit = -1;
+            }
+            s_vnext = 0;
             s_tcount = 0;
             s_skip = 0;
             s_chunk = 0;
@@ -257,6 +273,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         __syncthreads();
         const int32_t r = s_root;
         if (r < 0) break;
+        // part `part` of `nparts` of a split root: P members i with
+        // i % nparts == part and Q vertices b with b % nparts == part
+        const int32_t part = s_part >= 0 ? s_part : 0, nparts = s_part >= 0 ? A.split : 1;
         if (r < A.rank_lo || r >= A.rank_hi || r >= g.n) continue;
         const int64_t pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
         if (!in_bounds(g, pb >= 0 && pb <= pe && pe <= g.nnz && pe - pb <= A.lmax)) continue;
@@ -484,7 +503,12 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         }
 
         // ---- phase 5: per member v of P
-        for (int32_t i = warp; i < L; i += HUB_WARPS) {
+        for (;;) {
+            int32_t ii = 0;
+            if (lane == 0) ii = atomicAdd(&s_vnext, 1);
+            ii = __shfl_sync(0xffffffffu, ii, 0);
+            const int32_t i = part + nparts * ii;  // members in position order, largest first
+            if (i >= L) break;
             const uint32_t ev = __ldg(P + i);
             const uint32_t v = ev >> 2, al = ev & 3u;
             const int32_t h0 = hptr[i], h1 = hptr[i + 1];
@@ -862,8 +886,8 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 uint32_t b = 0u, nzm = 0u;
                 int64_t be = 0;
                 int32_t len = 0, o0 = 0, o1 = 0;
-                if (t < tcount) {
-                    b = (uint32_t)touched[t];
+                if (t < tcount) b = (uint32_t)touched[t];
+                if (t < tcount && (int32_t)(b % (uint32_t)nparts) == part) {
                     const int64_t bb = __ldg(g.rowptr + b);
                     be = __ldg(g.rowptr + b + 1);
                     len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
@@ -1032,12 +1056,33 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         // ---- phase 7: root credit, reset the slot
         {
             const int32_t orig = row_of(A.new2old, (uint32_t)r);
+            const bool ok = in_bounds(g, orig >= 0 && orig < g.n);
+            unsigned long long *out_r = (unsigned long long *)&A.out[(int64_t)orig * C];
+            // S1 sets are counted once per member of P: a split root's parts
+            // sum their partials, divided after the kernel (split_finish)
+            unsigned long long *acc = nparts > 1 ? A.split_acc + (int64_t)s_esplit * C : nullptr;
             for (int c = tid; c < C; c += HUB_THREADS) {
-                const unsigned long long v = hget(hP, c) / (K == 3 ? 2ull : 3ull) + hget(hD, c);
-                if (v && in_bounds(g, orig >= 0 && orig < g.n)) atomicAdd((unsigned long long *)&A.out[(int64_t)orig * C + c], v);
+                const unsigned long long p1 = hget(hP, c), d1 = hget(hD, c);
+                const unsigned long long v = (nparts == 1 ? p1 / (K == 3 ? 2ull : 3ull) : 0ull) + d1;
+                if (nparts > 1 && p1) atomicAdd(acc + c, p1);
+                if (v && ok) atomicAdd(out_r + c, v);
             }
         }
         reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
+    }
+}
+
+// root credit of the three-member sets of split roots: the parts' summed
+// partials / |P-members per set| (2 for k = 3, 3 for k = 4); one block per root
+__global__ void split_finish(const unsigned long long *__restrict__ acc, const int32_t *__restrict__ hubs,
+                             int32_t nsplit, int C, unsigned long long times, int64_t n, uint64_t *out) {
+    const int32_t e = blockIdx.x;
+    if (e >= nsplit) return;
+    const int32_t r = hubs[e];
+    if (r < 0 || r >= n) return;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const unsigned long long v = acc[(int64_t)e * C + c] / times;
+        if (v) atomicAdd((unsigned long long *)&out[(int64_t)r * C + c], v);
     }
 }
 
@@ -1098,6 +1143,9 @@ void vdmc_hub_free(vdmc_graph *g) {
     cudaFree(g->hubs);
     cudaFree(g->hub_scratch);
     cudaFree(g->hub_qhead);
+    cudaFree(g->hub_split_buf);
+    g->hub_split_buf = nullptr;
+    g->hub_split_cap = 0;
     g->hubs = nullptr;
     g->hub_scratch = nullptr;
     g->hub_qhead = nullptr;
@@ -1181,13 +1229,27 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
 int vdmc_hub_count(const vdmc_graph *g) { return g->nhubs; }
 
 vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
-                            int32_t hi, int blocks_per_sm, cudaStream_t s) {
+                            int32_t hi, int blocks_per_sm, int split, int split_roots, cudaStream_t s) {
     if (g->nhubs <= 0) return VDMC_OK;
     int dev = 0, sms = 0;
     VDMC_CUDA_TRY(cudaGetDevice(&dev));
     VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // the largest roots (first in the hub list) are split into `split` parts
+    const int C = k == 3 ? 13 : 199;
+    const int32_t nsplit = split > 1 ? std::min(split_roots, g->nhubs) : 0;
+    const int64_t queue = (int64_t)g->nhubs + (int64_t)nsplit * (split - 1);
+    const size_t split_bytes = (size_t)nsplit * sizeof(unsigned long long) * C;
+    if (nsplit > g->hub_split_cap) {
+        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(g->hub_split_buf);
+        g->hub_split_buf = nullptr;
+        g->hub_split_cap = 0;
+        VDMC_CUDA_TRY(cudaMalloc(&g->hub_split_buf, (size_t)nsplit * sizeof(unsigned long long) * 199));
+        g->hub_split_cap = nsplit;
+    }
+    if (nsplit > 0) VDMC_CUDA_TRY(cudaMemsetAsync(g->hub_split_buf, 0, split_bytes, s));
     int slots = std::max(1, sms * std::max(1, blocks_per_sm));
-    slots = std::min(slots, g->nhubs);
+    slots = (int)std::min<int64_t>(slots, queue);
     if (slots > g->hub_slots) {
         // (re)allocate the per-slot scratch; posmap starts at -1, counters at 0
         VDMC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1218,6 +1280,9 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     A.lut_g = lut;
     A.hubs = g->hubs;
     A.nhubs = g->nhubs;
+    A.nsplit = nsplit;
+    A.split = nsplit > 0 ? split : 1;
+    A.split_acc = (unsigned long long *)g->hub_split_buf;
     A.rank_lo = lo;
     A.rank_hi = hi;
     A.qhead = g->hub_qhead;
@@ -1249,5 +1314,9 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
         hub_kernel<4><<<(unsigned)slots, HUB_THREADS, dsmem, s>>>(A);
     }
     VDMC_CUDA_TRY(cudaGetLastError());
+    if (nsplit > 0) {
+        split_finish<<<(unsigned)nsplit, 256, 0, s>>>(A.split_acc, g->hubs, nsplit, C, k == 3 ? 2ull : 3ull, g->n, out);
+        VDMC_CUDA_TRY(cudaGetLastError());
+    }
     return VDMC_OK;
 }

@@ -56,6 +56,8 @@ struct vdmc_graph {
     void *hub_scratch;
     size_t hub_scratch_bytes;
     unsigned long long *hub_qhead;
+    void *hub_split_buf;         // split roots: nsplit * (C_k partial sums + a ticket)
+    int32_t hub_split_cap;
     cudaStream_t side;           // second stream: the two kernels overlap
     cudaEvent_t ev_fork, ev_join;
     uint64_t serial;             // creation number (identifies the graph in cached batch plans)
@@ -114,5 +116,5 @@ void vdmc_current_schedule(vdmc_schedule_t *s);
 // ---- root-per-CTA kernel (hub.cu) ----
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
 vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
-                            int32_t hi, int blocks_per_sm, cudaStream_t s);
+                            int32_t hi, int blocks_per_sm, int split, int split_roots, cudaStream_t s);
 void vdmc_hub_free(vdmc_graph *g);

@@ -80,8 +80,12 @@ def test_invalid_args_rejected_on_host(lib):
 def test_schedule_roundtrip(lib):
     old = vdmc.get_schedule()
     try:
-        vdmc.set_schedule(a_chunk=3, warps_per_block=4, blocks_per_sm=2, hub_min_l=7, hub_blocks_per_sm=2)
+        vdmc.set_schedule(a_chunk=3, warps_per_block=4, blocks_per_sm=2, hub_min_l=7, hub_blocks_per_sm=2,
+                          hub_split=4, hub_split_roots=9)
         assert vdmc.get_schedule() == {"a_chunk": 3, "warps_per_block": 4, "blocks_per_sm": 2,
-                                       "hub_min_l": 7, "hub_blocks_per_sm": 2}
+                                       "hub_min_l": 7, "hub_blocks_per_sm": 2, "hub_split": 4, "hub_split_roots": 9}
+        for bad in ({"hub_split": -1}, {"hub_split": 17}, {"hub_split_roots": -1}):
+            with pytest.raises(vdmc.VdmcError):
+                vdmc.set_schedule(**bad)
     finally:
         vdmc.set_schedule(**old)

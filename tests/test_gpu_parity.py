@@ -161,6 +161,44 @@ def test_schedules_do_not_change_results():
         vdmc.set_schedule(**old)
 
 
+@pytest.mark.parametrize("split,roots,hub", [(2, 5, 8), (3, 1000, 4), (4, 7, 1), (16, 3, 16), (5, 40, 2)])
+def test_split_roots_match_oracle(split, roots, hub):
+    # the largest roots counted by several CTAs (members and second-hop
+    # vertices shared out, three-member partials summed before the division)
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.chung_lu(1500, 4.0, 2.3, 5, reciprocity=0.2)
+    want = {k: O.count(n, s, d, k)[0] for k in (3, 4)}
+    old = vdmc.get_schedule()
+    try:
+        vdmc.set_schedule(hub_min_l=hub, hub_split=split, hub_split_roots=roots)
+        for k in (3, 4):
+            np.testing.assert_array_equal(gpu_count(n, s, d, k), want[k], err_msg="k=%d" % k)
+    finally:
+        vdmc.set_schedule(**old)
+
+
+def test_split_roots_with_rank_ranges():
+    # a root range that cuts through the split roots: every part of a root in
+    # range counts, every part of a root out of range skips
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.chung_lu(800, 5.0, 2.2, 9, reciprocity=0.3)
+    old = vdmc.get_schedule()
+    try:
+        vdmc.set_schedule(hub_min_l=0)
+        whole = gpu_count(n, s, d, 4)
+        vdmc.set_schedule(hub_min_l=4, hub_split=3, hub_split_roots=10)
+        with vdmc.graph_create(n, s, d) as g:
+            acc = torch.zeros((n, 199), dtype=torch.int64, device="cuda")
+            for lo, hi in ((0, 2), (2, 7), (7, 30), (30, n)):
+                part = vdmc.count_roots(g, 4, lo, hi)
+                acc += part.view(torch.int64)
+            torch.cuda.synchronize()
+            assert g.device_status() == 0
+        np.testing.assert_array_equal(acc.cpu().numpy().view(np.uint64), whole)
+    finally:
+        vdmc.set_schedule(**old)
+
+
 @pytest.fixture
 def schedule():
     from paper_2201_11655_b300 import vdmc
