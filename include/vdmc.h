@@ -86,7 +86,8 @@ typedef struct {
                                    takes a share of its members and second-hop
                                    vertices */
     int32_t hub_split_roots;    /* how many of the largest roots are split (>= 0) */
-    int32_t reserved[1];
+    int32_t hub_warps;          /* root-per-CTA kernel: warps per CTA, 16 or 32
+                                   (0 = 16) */
 } vdmc_schedule_t;
 
 /*

@@ -13,6 +13,7 @@ tests):
                      memory -- per-warp credit histograms -- grows with it)
   hub_split,         the largest hub_split_roots roots are each counted by
   hub_split_roots    hub_split CTAs (the critical path of fat-tailed graphs)
+  hub_warps          warps per CTA of the root-per-CTA kernel (16 or 32)
 
 The search is staged: the two root-per-CTA knobs first (they dominate on
 fat-tailed graphs), then the two warp-kernel knobs with the best of the
@@ -37,8 +38,9 @@ TUNED_PATH = os.path.join(HERE, "tuned_schedules.json")
 STAGE1 = ([{"hub_min_l": h, "hub_blocks_per_sm": b} for h in (1, 2, 4, 8, 16, 32, 64, 128, 256, 1024) for b in (1, 2)] +
           [{"hub_min_l": 0, "hub_blocks_per_sm": 1}])
 STAGE2 = [{"a_chunk": a, "warps_per_block": w} for a in (4, 16, 64) for w in (4, 8)]
-STAGE3 = ([{"hub_split": 1, "hub_split_roots": 0}] +
-          [{"hub_split": s, "hub_split_roots": r} for s, r in ((2, 32), (2, 64), (2, 128), (4, 16), (4, 48), (8, 12))])
+STAGE3 = ([{"hub_split": 1, "hub_split_roots": 0, "hub_warps": w} for w in (16, 32)] +
+          [{"hub_split": s, "hub_split_roots": r, "hub_warps": w} for s, r in ((2, 32), (2, 64), (4, 16), (8, 12))
+           for w in (16, 32)])
 
 
 def bucket(n: int, m: int) -> str:

@@ -41,7 +41,7 @@
 
 namespace {
 
-vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, {0}};
+vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, 16};
 std::mutex g_sched_mu;
 
 struct DevLut {
@@ -437,7 +437,7 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
         VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
         vdmc_status st = vdmc_hub_launch(g, k, acc, d3, lut, lo, hi, sch.hub_blocks_per_sm, sch.hub_split,
-                                          sch.hub_split_roots, g->side);
+                                          sch.hub_split_roots, sch.hub_warps, g->side);
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
     }
@@ -485,7 +485,7 @@ extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *byt
 extern "C" vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s) {
     if (!s || s->a_chunk < 1 || s->warps_per_block < 1 || s->warps_per_block > 8 || s->blocks_per_sm < 0 ||
         s->hub_min_l < 0 || s->hub_blocks_per_sm < 1 || s->hub_blocks_per_sm > 8 || s->hub_split < 0 ||
-        s->hub_split > 16 || s->hub_split_roots < 0)
+        s->hub_split > 16 || s->hub_split_roots < 0 || (s->hub_warps != 0 && s->hub_warps != 16 && s->hub_warps != 32))
         return VDMC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched = *s;

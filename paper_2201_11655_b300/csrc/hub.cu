@@ -48,12 +48,14 @@
 
 namespace {
 
-constexpr int HUB_WARPS = 16;
-constexpr int HUB_THREADS = HUB_WARPS * 32;
+// CTA size of the root-per-CTA kernel: 16 or 32 warps (template parameter W;
+// 32 warps hide more latency on large roots, 16 keep more registers and
+// suit many small roots)
 constexpr int32_t CLAIMED = -2;  // posmap: claimed, index being written
-// largest P bitmap kept in shared memory (next to ~37 KB of static shared
-// memory): 46,000 words = 184 KB, i.e. graphs of up to 1,472,000 vertices
-constexpr int64_t HUB_SMEM_BITS_MAX_WORDS = 46000;
+// largest P bitmap kept in shared memory next to the static shared memory
+// (~39 KB with 16 warps, ~70 KB with 32): 46,000 words = 184 KB (graphs of up
+// to 1,472,000 vertices) or 38,000 words = 152 KB (1,216,000 vertices)
+constexpr int64_t hub_smem_bits_max_words(int warps) { return warps == 32 ? 38000 : 46000; }
 
 struct HubArgs {
     Csr g;
@@ -136,7 +138,9 @@ __device__ __forceinline__ void sadd(const Hist64 &h, uint32_t cls, unsigned lon
 }
 
 // exclusive scan of hptr[0, L) in place (hptr[L] = total), whole CTA
+template <int HUB_WARPS>
 __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *total_out) {
+    constexpr int HUB_THREADS = HUB_WARPS * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t chunk = (L + HUB_THREADS - 1) / HUB_THREADS;
     const int32_t beg = min(L, tid * chunk), end = min(L, beg + chunk);
@@ -171,6 +175,7 @@ __device__ void cta_scan(int32_t *hptr, int32_t L, int32_t *warp_sums, int32_t *
 }
 
 // return the slot to its resting state (posmap -1, counters and bits 0)
+template <int HUB_THREADS>
 __device__ void reset_slot(int32_t *posmap, uint32_t *qcnt, const int32_t *touched, const uint32_t *P, int32_t L,
                            int32_t tcount, uint32_t *pbits, bool sbits, uint32_t *tbits) {
     for (int32_t p = threadIdx.x; p < L; p += HUB_THREADS) {
@@ -192,8 +197,9 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <int K>
-__global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args) {
+template <int K, int W>
+__global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
+    constexpr int HUB_WARPS = W, HUB_THREADS = W * 32;
     constexpr int C = (K == 3) ? 13 : 199;
     constexpr int NIDX = 1 << (K * (K - 1));
     __shared__ uint8_t lut[NIDX];
@@ -346,10 +352,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
         if (tcount > A.tcap) {
             if (tid == 0) s_skip = 1;
         }
-        cta_scan(hptr, L, warp_sums, &s_total);
+        cta_scan<HUB_WARPS>(hptr, L, warp_sums, &s_total);
         if (!in_bounds(g, s_total <= A.hcap && s_skip == 0)) {
             // leave the slot clean before giving up on this root
-            reset_slot(posmap, qcnt, touched, P, L, min(tcount, (int32_t)A.tcap), pbits, sbits, tbits);
+            reset_slot<HUB_THREADS>(posmap, qcnt, touched, P, L, min(tcount, (int32_t)A.tcap), pbits, sbits, tbits);
             continue;
         }
 
@@ -411,9 +417,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 npoff[t] = (int32_t)s9;
             }
             __syncthreads();
-            cta_scan(npoff, tcount, warp_sums, &s_total);
+            cta_scan<HUB_WARPS>(npoff, tcount, warp_sums, &s_total);
             if (!in_bounds(g, s_total <= A.npcap)) {
-                reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
+                reset_slot<HUB_THREADS>(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
                 continue;
             }
             // a warp takes a chunk of 32 Q vertices and walks their concatenated
@@ -1068,7 +1074,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 1) hub_kernel(const HubArgs args)
                 if (v && ok) atomicAdd(out_r + c, v);
             }
         }
-        reset_slot(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
+        reset_slot<HUB_THREADS>(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
     }
 }
 
@@ -1228,8 +1234,17 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
 
 int vdmc_hub_count(const vdmc_graph *g) { return g->nhubs; }
 
+template <int K, int W>
+cudaError_t launch_hub(int slots, size_t dsmem, const HubArgs &A, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(hub_kernel<K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+    if (e != cudaSuccess) return e;
+    hub_kernel<K, W><<<(unsigned)slots, W * 32, dsmem, s>>>(A);
+    return cudaGetLastError();
+}
+
 vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
-                            int32_t hi, int blocks_per_sm, int split, int split_roots, cudaStream_t s) {
+                            int32_t hi, int blocks_per_sm, int split, int split_roots, int warps, cudaStream_t s) {
+    warps = warps == 32 ? 32 : 16;
     if (g->nhubs <= 0) return VDMC_OK;
     int dev = 0, sms = 0;
     VDMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -1300,20 +1315,16 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     A.npcap = g->hub_npcap;
     A.tbits = (uint32_t *)(base + L.tbits);
     const int64_t words = ((int64_t)g->n + 31) / 32;
-    A.pbits_words = words <= HUB_SMEM_BITS_MAX_WORDS ? (int32_t)words : 0;
+    A.pbits_words = words <= hub_smem_bits_max_words(warps) ? (int32_t)words : 0;
     const size_t dsmem = (size_t)A.pbits_words * 4;
     A.tcap = g->hub_tcap;
     A.hcap = g->hub_hcap;
     A.lmax = g->hub_lmax;
     VDMC_CUDA_TRY(cudaMemsetAsync(g->hub_qhead, 0, sizeof(unsigned long long), s));
-    if (k == 3) {
-        VDMC_CUDA_TRY(cudaFuncSetAttribute(hub_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-        hub_kernel<3><<<(unsigned)slots, HUB_THREADS, dsmem, s>>>(A);
-    } else {
-        VDMC_CUDA_TRY(cudaFuncSetAttribute(hub_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-        hub_kernel<4><<<(unsigned)slots, HUB_THREADS, dsmem, s>>>(A);
-    }
-    VDMC_CUDA_TRY(cudaGetLastError());
+    cudaError_t le;
+    if (k == 3) le = warps == 32 ? launch_hub<3, 32>(slots, dsmem, A, s) : launch_hub<3, 16>(slots, dsmem, A, s);
+    else le = warps == 32 ? launch_hub<4, 32>(slots, dsmem, A, s) : launch_hub<4, 16>(slots, dsmem, A, s);
+    VDMC_CUDA_TRY(le);
     if (nsplit > 0) {
         split_finish<<<(unsigned)nsplit, 256, 0, s>>>(A.split_acc, g->hubs, nsplit, C, k == 3 ? 2ull : 3ull, g->n, out);
         VDMC_CUDA_TRY(cudaGetLastError());

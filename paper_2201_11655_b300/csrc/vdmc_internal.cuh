@@ -116,5 +116,6 @@ void vdmc_current_schedule(vdmc_schedule_t *s);
 // ---- root-per-CTA kernel (hub.cu) ----
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
 vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
-                            int32_t hi, int blocks_per_sm, int split, int split_roots, cudaStream_t s);
+                            int32_t hi, int blocks_per_sm, int split, int split_roots, int warps,
+                            cudaStream_t s);
 void vdmc_hub_free(vdmc_graph *g);

@@ -45,10 +45,10 @@ class Schedule(ctypes.Structure):
     _fields_ = [("a_chunk", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hub_min_l", ctypes.c_int32),
                 ("hub_blocks_per_sm", ctypes.c_int32), ("hub_split", ctypes.c_int32),
-                ("hub_split_roots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("hub_split_roots", ctypes.c_int32), ("hub_warps", ctypes.c_int32)]
 
 SCHEDULE_KEYS = ("a_chunk", "warps_per_block", "blocks_per_sm", "hub_min_l", "hub_blocks_per_sm", "hub_split",
-                 "hub_split_roots")
+                 "hub_split_roots", "hub_warps")
 
 
 _LIB = None

@@ -161,16 +161,23 @@ def test_schedules_do_not_change_results():
         vdmc.set_schedule(**old)
 
 
-@pytest.mark.parametrize("split,roots,hub", [(2, 5, 8), (3, 1000, 4), (4, 7, 1), (16, 3, 16), (5, 40, 2)])
-def test_split_roots_match_oracle(split, roots, hub):
+_SPLIT_GRAPH = {}
+
+
+@pytest.mark.parametrize("warps", [16, 32])
+@pytest.mark.parametrize("split,roots,hub", [(1, 0, 8), (2, 5, 8), (3, 1000, 4), (4, 7, 1), (16, 3, 16), (5, 40, 2)])
+def test_split_roots_match_oracle(split, roots, hub, warps):
     # the largest roots counted by several CTAs (members and second-hop
-    # vertices shared out, three-member partials summed before the division)
+    # vertices shared out, three-member partials summed before the division),
+    # with 16- and 32-warp CTAs
     from paper_2201_11655_b300 import vdmc
-    n, s, d = synth.chung_lu(1500, 4.0, 2.3, 5, reciprocity=0.2)
-    want = {k: O.count(n, s, d, k)[0] for k in (3, 4)}
+    if not _SPLIT_GRAPH:
+        n, s, d = synth.chung_lu(1500, 4.0, 2.3, 5, reciprocity=0.2)
+        _SPLIT_GRAPH.update(n=n, s=s, d=d, want={k: O.count(n, s, d, k)[0] for k in (3, 4)})
+    n, s, d, want = _SPLIT_GRAPH["n"], _SPLIT_GRAPH["s"], _SPLIT_GRAPH["d"], _SPLIT_GRAPH["want"]
     old = vdmc.get_schedule()
     try:
-        vdmc.set_schedule(hub_min_l=hub, hub_split=split, hub_split_roots=roots)
+        vdmc.set_schedule(hub_min_l=hub, hub_split=split, hub_split_roots=roots, hub_warps=warps)
         for k in (3, 4):
             np.testing.assert_array_equal(gpu_count(n, s, d, k), want[k], err_msg="k=%d" % k)
     finally:
