@@ -36,8 +36,13 @@
 // Work per root is O(sum of the degrees of P and of its Q-neighbours +
 // enumerated exceptions) instead of O(number of sets).  Each CTA owns a
 // slot of scratch: a rank-indexed position map (-1 = not yet seen), compact
-// per-Q-vertex counters, the adjacency lists of H.  Waits: none; the only
-// cross-thread protocol is claim-by-atomicCAS followed by a barrier.
+// per-Q-vertex counters, the adjacency lists of H.  The rows of the Q
+// vertices are walked by warps taking chunks of Q vertices, lanes on
+// consecutive entries of the chunk's concatenated rows.  The largest roots
+// can be split across several CTAs (members of P and Q vertices shared out
+// by position / id; the three-member partials summed and divided by a
+// finishing kernel).  Waits: none; the only cross-thread protocols are
+// claim-by-atomicCAS followed by a barrier and work claims by atomicAdd.
 #include <cuda_runtime.h>
 
 #include <algorithm>
