@@ -553,34 +553,71 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                     sadd(hP, cls, 1ull);
                 }
             } else {
-                // -- S1 per-member counts: H-edges inside R_v = P \ N_H[v] by type
+                // -- S1 per-member counts: H-edges inside R_v = P \ N_H[v] by type,
+                // and H-neighbours w shared by v and u in NH(v) (S1 with the one
+                // H-edge (v,u), third member w adjacent to both: corrected per w).
+                // Lanes walk the concatenated H-lists of N_H[v] = {v} + NH(v) in
+                // chunks of 32 owners (owner j = -1 is v itself).
                 for (int k = lane; k < 27; k += 32) {
                     esub[warp][k] = 0u;
                     eins[warp][k] = 0u;
                 }
                 __syncwarp();
-                // light H-neighbours (short H-lists): one per lane; heavy ones:
-                // the whole warp walks the list
-                for (int pass = 0; pass < 2; pass++) {
-                    const int32_t jstart = pass == 0 ? lane - 1 : -1;
-                    const int32_t jstep = pass == 0 ? 32 : 1;
-                    for (int32_t j = jstart; j < dH; j += jstep) {
-                        const uint32_t up = j < 0 ? (uint32_t)i : (hlist[h0 + j] >> 2);
-                        const int32_t u0 = hptr[up], u1 = hptr[up + 1];
-                        const bool heavy = (u1 - u0) > 32;
-                        if (heavy != (pass == 1)) continue;
-                        const uint32_t cu = __ldg(P + up) & 3u;
-                        const int32_t k0 = pass == 0 ? u0 : u0 + lane, ks = pass == 0 ? 1 : 32;
-                        for (int32_t k = k0; k < u1; k += ks) {
-                            const uint32_t ew = hlist[k];
-                            const uint32_t w = ew >> 2;
-                            const int t = etype(cu, __ldg(P + w) & 3u, ew & 3u);
-                            atomicAdd(&esub[warp][t], 1u);
-                            if (up < w) {
-                                const bool inside = (up == (uint32_t)i) || (w == (uint32_t)i) ||
-                                                    hlist_find(hlist, h0, h1, w) != 0u;
-                                if (inside) atomicAdd(&eins[warp][t], 1u);
+                for (int32_t j0 = -1; j0 < dH; j0 += 32) {
+                    const int32_t j = j0 + lane;
+                    uint32_t up = 0u, fvu = 0u, cu = 0u;
+                    int32_t u0 = 0, len = 0;
+                    if (j < dH) {
+                        const uint32_t eu = j < 0 ? ((uint32_t)i << 2) : hlist[h0 + j];
+                        up = eu >> 2;
+                        fvu = j < 0 ? 0u : (eu & 3u);
+                        cu = __ldg(P + up) & 3u;
+                        u0 = hptr[up];
+                        len = hptr[up + 1] - u0;
+                        if (j >= 0) {
+                            // S1 one H-edge (v,u), third member isolated from both, by its
+                            // colour (the shared H-neighbours are added back per w below)
+#pragma unroll
+                            for (uint32_t ga = 1; ga <= 3; ga++) {
+                                const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - hcx[up * 3 + ga - 1];
+                                const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
+                                sadd(hvh, cls, (unsigned long long)cnt);
+                                sadd(hP, cls, (unsigned long long)cnt);
                             }
+                        }
+                    }
+                    int32_t incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    for (int32_t base = 0; base < total; base += 32) {
+                        const int32_t jj = base + lane;
+                        int32_t w = 0;
+#pragma unroll
+                        for (int sh = 16; sh >= 1; sh >>= 1)
+                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= jj) w += sh;
+                        const uint32_t upo = __shfl_sync(0xffffffffu, up, w);
+                        const uint32_t cuo = __shfl_sync(0xffffffffu, cu, w);
+                        const uint32_t fvo = __shfl_sync(0xffffffffu, fvu, w);
+                        const int32_t u0o = __shfl_sync(0xffffffffu, u0, w);
+                        const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                        const int32_t leno = __shfl_sync(0xffffffffu, len, w);
+                        if (jj >= total) continue;
+                        const uint32_t ew = hlist[u0o + (jj - (io - leno))];
+                        const uint32_t wp = ew >> 2;
+                        const uint32_t cw = __ldg(P + wp) & 3u;
+                        const int t = etype(cuo, cw, ew & 3u);
+                        atomicAdd(&esub[warp][t], 1u);
+                        const bool vside = upo == (uint32_t)i || wp == (uint32_t)i;
+                        const bool inh = !vside && hlist_find(hlist, h0, h1, wp) != 0u;  // w in NH(v)
+                        if (upo < wp && (vside || inh)) atomicAdd(&eins[warp][t], 1u);
+                        if (inh) {
+                            const uint32_t cls = lut[mask4(al, cuo, cw, fvo, 0u, 0u)];
+                            sadd(hvh, cls, 1ull);
+                            sadd(hP, cls, 1ull);
                         }
                     }
                 }
@@ -610,94 +647,87 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                     sadd(hvh, cls, (unsigned long long)pairs);
                     sadd(hP, cls, (unsigned long long)pairs);
                 }
-                // -- per H-neighbour u of v (light u: one per lane; heavy u: the
-                // whole warp shares its lists)
+                // -- S2 across each H-edge (v,u), handled once by the endpoint of
+                // larger degree: common Q-neighbours c of v and u.  Lanes walk the
+                // concatenated upper rows of the u handled from v, 32 u per chunk.
                 const int64_t dv = ve - vb;
                 const bool vshort = ve - vu <= 256;
-                for (int pass = 0; pass < 2; pass++) {
-                    const int32_t jstart = pass == 0 ? lane : 0, jstep = pass == 0 ? 32 : 1;
-                    for (int32_t j = jstart; j < dH; j += jstep) {
+                for (int32_t j0 = 0; j0 < dH; j0 += 32) {
+                    const int32_t j = j0 + lane;
+                    uint32_t u = 0u, cu = 0u, fvu = 0u;
+                    int64_t ue = 0;
+                    int32_t len = 0;
+                    if (j < dH) {
                         const uint32_t eu = hlist[h0 + j];
-                        const uint32_t up = eu >> 2, fvu = eu & 3u;
-                        const uint32_t u = __ldg(P + up) >> 2, cu = __ldg(P + up) & 3u;
-                        const int32_t u0 = hptr[up], u1 = hptr[up + 1];
-                        const int64_t ub = __ldg(g.rowptr + u), ue = __ldg(g.rowptr + u + 1);
+                        const uint32_t up = eu >> 2;
+                        fvu = eu & 3u;
+                        const uint32_t pu = __ldg(P + up);
+                        u = pu >> 2;
+                        cu = pu & 3u;
+                        const int64_t ub = __ldg(g.rowptr + u);
+                        ue = __ldg(g.rowptr + u + 1);
                         const int64_t du = ue - ub;
-                        const bool heavy = (u1 - u0) > 32 || du > 64;
-                        if (heavy != (pass == 1)) continue;
-                        const bool coop = pass == 1;
-                        const int32_t ls = coop ? lane : 0, st = coop ? 32 : 1;
-                        uint32_t com0 = 0, com1 = 0, com2 = 0;
-                        for (int32_t k = u0 + ls; k < u1; k += st) {
-                            const uint32_t w = hlist[k] >> 2;
-                            if (w != (uint32_t)i && hlist_find(hlist, h0, h1, w)) {
-                                const uint32_t cw = __ldg(P + w) & 3u;
-                                com0 += cw == 1u; com1 += cw == 2u; com2 += cw == 3u;
-                            }
-                        }
-                        if (coop) {
-                            com0 = warp_sum(com0); com1 = warp_sum(com1); com2 = warp_sum(com2);
-                        }
-                        const uint32_t com[3] = {com0, com1, com2};
-                        // S1 one H-edge (v,u), third member isolated, by its colour
-                        if (!coop || lane == 0) {
-                            for (uint32_t ga = 1; ga <= 3; ga++) {
-                                const long long cnt = (long long)ncol[ga - 1] - hcv[ga - 1] - hcx[up * 3 + ga - 1] + com[ga - 1];
-                                const uint32_t cls = lut[mask4(al, cu, ga, fvu, 0u, 0u)];
-                                sadd(hvh, cls, (unsigned long long)cnt);
-                                sadd(hP, cls, (unsigned long long)cnt);
-                            }
-                        }
-                        // S2 across the H-edge (v,u), handled once by the endpoint of
-                        // larger degree: common Q-neighbours c of v and u
-                        if (!(dv > du || (dv == du && (uint32_t)i < up))) continue;
-                        uint32_t cqv0 = 0, cqv1 = 0, cqv2 = 0, cqu0 = 0, cqu1 = 0, cqu2 = 0;
-                        const uint32_t fuv = swapf(fvu);
-                        // scan u's Q-neighbours (u has the smaller degree); v in NP(c)?
-                        for (int64_t e = upper_row(g.col, ub, ue, (uint32_t)r) + ls; e < ue; e += st) {
-                            const uint32_t ec = __ldg(g.col + e);
-                            const uint32_t c = ec >> 2;
-                            if (in_P(c)) continue;
-                            // h(v, c): a search of v's upper row when it is short (it
-                            // stays in L1), else the position of v in NP(c)
-                            uint32_t fvc;
-                            if (vshort) {
-                                fvc = search_row(g.col, vu, ve, c);
-                            } else {
-                                const int32_t pc = __ldcg(posmap + c);
-                                if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
-                                const int64_t tc = -3 - (int64_t)pc;
-                                fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
-                            }
-                            if (!fvc) continue;
-                            const uint32_t fuc = ec & 3u;
-                            cqv0 += fvc == 1u; cqv1 += fvc == 2u; cqv2 += fvc == 3u;
-                            cqu0 += fuc == 1u; cqu1 += fuc == 2u; cqu2 += fuc == 3u;
-                            // both adjacent to c and to each other: enumerate, and take
-                            // the pair out of c's non-adjacent-pair count
-                            const uint32_t cle = lut[mask4(al, cu, 0u, fvu, fvc, fuc)];
-                            const uint32_t clb = lut[mask4(al, cu, 0u, 0u, fvc, fuc)];
-                            sadd(hvh, cle, 1ull);
-                            gadd(S, u, cle, 1ull, C);
-                            gadd(S, c, cle, 1ull, C);
-                            sadd(hD, cle, 1ull);
-                            sadd(hvh, clb, ~0ull);
-                            gadd(S, u, clb, ~0ull, C);
-                            gadd(S, c, clb, ~0ull, C);
-                            sadd(hD, clb, ~0ull);
-                        }
-                        if (coop) {
-                            cqv0 = warp_sum(cqv0); cqv1 = warp_sum(cqv1); cqv2 = warp_sum(cqv2);
-                            cqu0 = warp_sum(cqu0); cqu1 = warp_sum(cqu1); cqu2 = warp_sum(cqu2);
-                        }
-                        const uint32_t cqv[3] = {cqv0, cqv1, cqv2}, cqu[3] = {cqu0, cqu1, cqu2};
-                        // S2 credit of u for c in NQ(v) \ N(u) and of v for c in NQ(u) \ N(v)
-                        if (!coop || lane == 0) {
+                        if (dv > du || (dv == du && (uint32_t)i < up)) {
+                            len = (int32_t)(ue - upper_row(g.col, ub, ue, (uint32_t)r));
+                            // S2 credit of u for c in NQ(v) and of v for c in NQ(u), as if no
+                            // c were adjacent to both (taken back per common c below)
+                            const uint32_t fuv = swapf(fvu);
+#pragma unroll
                             for (uint32_t f = 1; f <= 3; f++) {
-                                gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)(Wv[f - 1] - cqv[f - 1]), C);
-                                sadd(hvh, lut[mask4(cu, al, 0u, fuv, f, 0u)], (unsigned long long)(wx[up * 3 + f - 1] - cqu[f - 1]));
+                                gadd(S, u, lut[mask4(al, cu, 0u, fvu, f, 0u)], (unsigned long long)Wv[f - 1], C);
+                                sadd(hvh, lut[mask4(cu, al, 0u, fuv, f, 0u)], (unsigned long long)wx[up * 3 + f - 1]);
                             }
                         }
+                    }
+                    int32_t incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    for (int32_t base = 0; base < total; base += 32) {
+                        const int32_t jj = base + lane;
+                        int32_t w = 0;
+#pragma unroll
+                        for (int sh = 16; sh >= 1; sh >>= 1)
+                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= jj) w += sh;
+                        const uint32_t uo = __shfl_sync(0xffffffffu, u, w);
+                        const uint32_t cuo = __shfl_sync(0xffffffffu, cu, w);
+                        const uint32_t fvo = __shfl_sync(0xffffffffu, fvu, w);
+                        const int64_t ueo = __shfl_sync(0xffffffffu, ue, w);
+                        const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                        if (jj >= total) continue;
+                        const uint32_t ec = __ldg(g.col + (ueo - (int64_t)(io - jj)));  // u's upper row ends at ue
+                        const uint32_t c = ec >> 2;
+                        if (in_P(c)) continue;
+                        // h(v, c): a search of v's upper row when it is short (it stays
+                        // in L1), else the position of v in NP(c)
+                        uint32_t fvc;
+                        if (vshort) {
+                            fvc = search_row(g.col, vu, ve, c);
+                        } else {
+                            const int32_t pc = __ldcg(posmap + c);
+                            if (!in_bounds(g, pc <= -3 && (-3 - (int64_t)pc) < tcount)) continue;
+                            const int64_t tc = -3 - (int64_t)pc;
+                            fvc = hlist_find(nplist, npoff[tc], npoff[tc + 1], (uint32_t)i);
+                        }
+                        if (!fvc) continue;
+                        const uint32_t fuc = ec & 3u;
+                        // both adjacent to c and to each other: enumerate, and take the
+                        // pair out of the bulk counts
+                        const uint32_t cle = lut[mask4(al, cuo, 0u, fvo, fvc, fuc)];
+                        const uint32_t clb = lut[mask4(al, cuo, 0u, 0u, fvc, fuc)];
+                        sadd(hvh, cle, 1ull);
+                        gadd(S, uo, cle, 1ull, C);
+                        gadd(S, c, cle, 1ull, C);
+                        sadd(hD, cle, 1ull);
+                        sadd(hvh, clb, ~0ull);
+                        gadd(S, uo, clb, ~0ull, C);
+                        gadd(S, c, clb, ~0ull, C);
+                        sadd(hD, clb, ~0ull);
+                        gadd(S, uo, lut[mask4(al, cuo, 0u, fvo, fvc, 0u)], ~0ull, C);
+                        sadd(hvh, lut[mask4(cuo, al, 0u, swapf(fvo), fuc, 0u)], ~0ull);
                     }
                 }
                 // -- S1 sets with two or three H-edges, v the centre
