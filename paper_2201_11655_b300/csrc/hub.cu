@@ -730,13 +730,19 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         sadd(hvh, lut[mask4(cuo, al, 0u, swapf(fvo), fuc, 0u)], ~0ull);
                     }
                 }
-                // -- S1 sets with two or three H-edges, v the centre
-                for (int32_t j1 = 0; j1 < dH; j1++) {
-                    const uint32_t e1 = hlist[h0 + j1];
-                    const uint32_t yp = e1 >> 2, fvy = e1 & 3u;
-                    const uint32_t cy = __ldg(P + yp) & 3u;
-                    const int32_t y0 = hptr[yp], y1 = hptr[yp + 1];
-                    for (int32_t j2 = j1 + 1 + lane; j2 < dH; j2 += 32) {
+                // -- S1 sets with two or three H-edges, v the centre: lanes over the
+                // pairs (j1 < j2) of NH(v) in row order, lane l on pairs l, l+32, ...
+                {
+                    int32_t j1 = 0, j2 = 1 + lane;
+                    while (j1 < dH - 1 && j2 >= dH) {  // carry into the next row
+                        j1++;
+                        j2 = j2 - dH + j1 + 1;
+                    }
+                    for (; j1 < dH - 1;) {
+                        const uint32_t e1 = hlist[h0 + j1];
+                        const uint32_t yp = e1 >> 2, fvy = e1 & 3u;
+                        const uint32_t cy = __ldg(P + yp) & 3u;
+                        const int32_t y0 = hptr[yp], y1 = hptr[yp + 1];
                         const uint32_t e2 = hlist[h0 + j2];
                         const uint32_t zp = e2 >> 2, fvz = e2 & 3u;
                         const uint32_t cz = __ldg(P + zp) & 3u;
@@ -747,6 +753,11 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                             gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
                             gadd(S, __ldg(P + zp) >> 2, cls, 1ull, C);
                             sadd(hP, cls, 3ull);
+                        }
+                        j2 += 32;
+                        while (j1 < dH - 1 && j2 >= dH) {
+                            j1++;
+                            j2 = j2 - dH + j1 + 1;
                         }
                     }
                 }
