@@ -77,7 +77,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("count.cu", "vdmc_internal.cuh"):
+    for name in ("hub.cu", "count.cu", "device_common.cuh", "vdmc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2201_11655_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
