@@ -261,16 +261,19 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
 }
 
 // out[new2old[r]] = acc[r] (+ the depth-3 credits d3[r], k = 4), one warp
-// per row (coalesced row copies).  Column j = 3 * type + flag - 1 of d3
-// holds sets r' - x - b - c credited to c: type = (colour of x, h(x, b)),
-// flag = h(b, c); its class is that of mask4(colour, 0, 0, h(x,b), 0, h(b,c)).
+// per row (coalesced row copies).  Column d of d3 holds the sets r' - x - b - c
+// credited to c whose class is the d-th smallest of the depth-3 path classes
+// (d3_column); unused columns stay zero.
 __global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ d3,
                                const uint8_t *__restrict__ lut, const int32_t *__restrict__ new2old, int32_t n,
                                int C, uint64_t *__restrict__ out) {
-    __shared__ uint8_t d3cls[27];
+    __shared__ int d3cls[VDMC_D3_COLS];
+    if (threadIdx.x < VDMC_D3_COLS) d3cls[threadIdx.x] = -1;
+    __syncthreads();
     if (d3 && threadIdx.x < 27) {
-        const uint32_t j = threadIdx.x, k = j / 3;
-        d3cls[j] = lut[mask4(k / 3 + 1, 0u, 0u, k % 3 + 1, 0u, j % 3 + 1)];
+        int cls = 0;
+        const int col = d3_column(lut, threadIdx.x, &cls);
+        if (col < VDMC_D3_COLS) d3cls[col] = cls;  // equal types write the same class
     }
     __syncthreads();
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -281,8 +284,8 @@ __global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t 
     for (int c = lane; c < C; c += 32) {
         uint64_t v = acc[r * C + c];
         if (d3) {
-            for (int j = 0; j < 27; j++)
-                if (d3cls[j] == c) v += d3[r * 27 + j];
+            for (int j = 0; j < VDMC_D3_COLS; j++)
+                if (d3cls[j] == c) v += d3[r * VDMC_D3_COLS + j];
         }
         out[(int64_t)o * C + c] = v;
     }
@@ -417,16 +420,16 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     }
     uint64_t *acc = g->racc;
     if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
-    // depth-3 credits of the root-per-CTA kernel (k = 4): 27 columns per
-    // vertex instead of 199, so that their reductions mostly stay in L2
+    // depth-3 credits of the root-per-CTA kernel (k = 4): one column per path
+    // class (16 per vertex) instead of 199, so that more reductions stay in L2
     uint64_t *d3 = nullptr;
     if (k == 4 && g->nhubs > 0 && g->n > 0) {
         if (!g->d3acc) {
             VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-            VDMC_CUDA_TRY(cudaMalloc((void **)&g->d3acc, sizeof(uint64_t) * (size_t)g->n * 27));
+            VDMC_CUDA_TRY(cudaMalloc((void **)&g->d3acc, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS));
         }
         d3 = g->d3acc;
-        VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, sizeof(uint64_t) * (size_t)g->n * 27, s));
+        VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
     }
     const uint8_t *lut = nullptr;
     VDMC_CUDA_TRY(device_lut(k, &lut));

@@ -96,6 +96,26 @@ __device__ __forceinline__ uint32_t mask4(uint32_t fra, uint32_t frb, uint32_t f
            ((fac >> 1) << 1) | (fbc >> 1);
 }
 
+// Column of the depth-3 credit type j = 3 * type + flag - 1 (type = 3 *
+// (colour - 1) + h(x, b) - 1, flag = h(b, c)): the rank of its class among the
+// distinct classes of the 27 types.  *cls_out gets the class itself.
+__device__ __forceinline__ int d3_column(const uint8_t *lut, int j, int *cls_out) {
+    auto cls_of = [&](int t) {
+        const uint32_t k = (uint32_t)t / 3;
+        return (int)lut[mask4(k / 3 + 1, 0u, 0u, k % 3 + 1, 0u, (uint32_t)t % 3 + 1)];
+    };
+    const int c = cls_of(j);
+    int rank = 0;
+    for (int i = 0; i < 27; i++) {
+        const int ci = cls_of(i);
+        bool first = ci < c;
+        for (int m = 0; m < i && first; m++) first = cls_of(m) != ci;
+        rank += first ? 1 : 0;
+    }
+    *cls_out = c;
+    return rank;
+}
+
 // Output row of vertex (rank) v: its original id through the id map, or v
 // itself when the kernel accumulates in rank space (map == nullptr; the
 // rows are permuted to original ids afterwards).

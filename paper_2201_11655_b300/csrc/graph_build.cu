@@ -440,7 +440,7 @@ extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *i
     info->num_hub_roots = g->nhubs;
     info->device_bytes += (int64_t)g->hub_scratch_bytes;
     if (g->racc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES);
-    if (g->d3acc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * 27);
+    if (g->d3acc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS);
     return VDMC_OK;
 }
 

@@ -66,7 +66,7 @@ struct HubArgs {
     Csr g;
     const int32_t *new2old;
     uint64_t *out;
-    unsigned long long *d3;  // k = 4: n * 27 depth-3 credits (rank space)
+    unsigned long long *d3;  // k = 4: n * VDMC_D3_COLS depth-3 credits (rank space)
     const uint8_t *lut_g;
     const int32_t *hubs;
     int32_t nhubs;
@@ -250,6 +250,12 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
     const Hist64 hE = hist64(Etype, 27), hW = hist64(Wtot, 9);
 
     for (int i = tid; i < NIDX; i += HUB_THREADS) lut[i] = A.lut_g[i];
+    __shared__ uint8_t d3col[27];  // depth-3 credit type -> column (k = 4)
+    __syncthreads();
+    if (K == 4 && tid < 27) {
+        int cls = 0;
+        d3col[tid] = (uint8_t)min(d3_column(lut, tid, &cls), VDMC_D3_COLS - 1);
+    }
     for (int i = tid; i < A.pbits_words; i += HUB_THREADS) pbits[i] = 0u;
     for (int i = tid; i < HUB_WARPS * C; i += HUB_THREADS) (&whist[0][0])[i] = 0ull;
 
@@ -1073,12 +1079,13 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                     bool cand = false;
                     if (j < total && !in_P(c)) {
                         // S4 credit of c (b at depth 2, c at depth 3), in c's
-                        // depth-3 columns (type of x, h(b, c))
+                        // depth-3 column of the class of (type of x, h(b, c))
                         if (nzo && in_bounds(g, c < (uint32_t)g.n && gg != 0u)) {
 #pragma unroll
                             for (int k = 0; k < 9; k++)
                                 if ((nzo >> k) & 1u)
-                                    atomicAdd(A.d3 + (int64_t)c * 27 + k * 3 + gg - 1, (unsigned long long)sq[w * 9 + k]);
+                                    atomicAdd(A.d3 + (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1],
+                                              (unsigned long long)sq[w * 9 + k]);
                         }
                         cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
                     }

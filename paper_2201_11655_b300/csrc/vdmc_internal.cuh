@@ -64,8 +64,14 @@ struct vdmc_graph {
     int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
     uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
-    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * 27 (rank space)
+    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * VDMC_D3_COLS (rank space)
 };
+
+// Depth-3 credit columns per vertex (k = 4, root-per-CTA kernel): the paths
+// r - x - b - c credited to c are typed by (colour of x, h(x, b), h(b, c)),
+// 27 types in 15 classes (a path and its reverse are isomorphic); one column
+// per class, 16 columns = one 128-byte line per vertex.
+constexpr int VDMC_D3_COLS = 16;
 
 // ---- status helpers ----
 #define VDMC_CUDA_TRY(expr)                                         \
