@@ -395,8 +395,9 @@ def run_ours(args):
     achieved = wbytes / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": load_traffic(args.workload, k),
-                "kernel": "vdmc_count: hub_kernel<%d> (root-per-CTA) overlapped with count_kernel<%d> "
-                          "(warp-per-task), timed together" % (k, k),
+                "kernel": "vdmc_count: hub_kernel<%d, %d warps> (root-per-CTA) overlapped with count_kernel<%d> "
+                          "(warp-per-task), timed together; traffic = DRAM bytes of all kernels of one count"
+                          % (k, vdmc.get_schedule()["hub_warps"] or 16, k),
                 "algorithmic_bytes_per_launch": wbytes, "peak_kind": "%s hbm_gbs (copy)" % peak_kind}
 
     cpu = None
