@@ -212,10 +212,14 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
     __shared__ unsigned long long whist[HUB_WARPS][C];
     __shared__ uint32_t esub[HUB_WARPS][27], eins[HUB_WARPS][27];
     __shared__ uint32_t vq[HUB_WARPS][32];  // queued Q entries of a P member's row
+    // per-member counters of phases 2 and 3 (k = 4 keeps them in the warp's
+    // histogram, which is too small for them at k = 3)
+    static_assert(K == 3 || 2 * C >= 32 * 10, "member counters must fit the warp histogram");
+    __shared__ uint32_t mscr[HUB_WARPS][K == 3 ? 32 * 10 : 1];
     __shared__ unsigned long long Etype[27];
     __shared__ unsigned long long Wtot[9];
     __shared__ uint32_t ncol[3];
-    __shared__ int32_t s_root, s_part, s_esplit, s_tcount, s_total, s_skip, s_chunk, s_chunk4, s_vnext;
+    __shared__ int32_t s_root, s_part, s_esplit, s_tcount, s_total, s_skip, s_chunk, s_chunk2, s_chunk3, s_chunk4, s_vnext;
     __shared__ int32_t warp_sums[32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -275,6 +279,8 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                 s_esplit = -1;
             }
             s_vnext = 0;
+            s_chunk2 = 0;
+            s_chunk3 = 0;
             s_tcount = 0;
             s_skip = 0;
             s_chunk = 0;
@@ -309,30 +315,57 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
         __syncthreads();
 
         // ---- phase 2: per x in P: |NH(x)|, colours of NH(x), |NQ(x)| by flag;
-        // claim the Q vertices (compact index per Q vertex)
-        // light x (short rows): one per thread; heavy x: one per warp
-        for (int pass = 0; pass < 2; pass++) {
-            const bool coop = pass == 1;
-            for (int32_t i = coop ? warp : tid; i < L; i += coop ? HUB_WARPS : HUB_THREADS) {
-                const uint32_t x = __ldg(P + i) >> 2;
-                const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
-                if ((xe - xb > 32) != coop) continue;
-                const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
-                uint32_t dh = 0, hc0 = 0, hc1 = 0, hc2 = 0, w0 = 0, w1 = 0, w2 = 0;
-                for (int64_t e = xu + (coop ? lane : 0); e < xe; e += coop ? 32 : 1) {
-                    const uint32_t ent = __ldg(g.col + e);
+        // claim the Q vertices (compact index per Q vertex).  A warp takes a
+        // chunk of members (32, fewer when P is small) and walks their
+        // concatenated upper rows, lanes on consecutive entries.
+        const int32_t psz = max(1, min(32, L / (HUB_WARPS * 4)));
+        {
+            // [7][32] per member of the chunk: |NH(x)|, NH(x) by colour, NQ(x) by
+            // flag -- in the warp's histogram (k = 4) or a small array (k = 3)
+            uint32_t *cnt = K == 4 ? reinterpret_cast<uint32_t *>(hv) : mscr[warp];
+            for (;;) {
+                int32_t c0 = 0;
+                if (lane == 0) c0 = atomicAdd(&s_chunk2, psz);
+                c0 = __shfl_sync(0xffffffffu, c0, 0);
+                if (c0 >= L) break;
+                const int32_t i = lane < psz ? c0 + lane : L;
+                int64_t xe = 0;
+                int32_t len = 0;
+                if (i < L) {
+                    const uint32_t x = __ldg(P + i) >> 2;
+                    const int64_t xb = __ldg(g.rowptr + x);
+                    xe = __ldg(g.rowptr + x + 1);
+                    len = (int32_t)(xe - upper_row(g.col, xb, xe, (uint32_t)r));
+                }
+#pragma unroll
+                for (int m = 0; m < 7; m++) cnt[m * 32 + lane] = 0u;
+                int32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                for (int32_t base = 0; base < total; base += 32) {
+                    const int32_t jj = base + lane;
+                    int32_t w = 0;
+#pragma unroll
+                    for (int sh = 16; sh >= 1; sh >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= jj) w += sh;
+                    const int64_t xeo = __shfl_sync(0xffffffffu, xe, w);
+                    const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                    if (jj >= total) continue;
+                    const uint32_t ent = __ldg(g.col + (xeo - (int64_t)(io - jj)));  // x's upper row ends at xe
                     const uint32_t u = ent >> 2, f = ent & 3u;
                     if (in_P(u)) {
                         const int32_t p = __ldcg(posmap + u);
-                        dh++;
+                        if (!in_bounds(g, p >= 0 && p < L)) continue;
                         const uint32_t cu = __ldg(P + p) & 3u;
-                        hc0 += cu == 1u;
-                        hc1 += cu == 2u;
-                        hc2 += cu == 3u;
+                        atomicAdd(&cnt[w], 1u);
+                        atomicAdd(&cnt[cu * 32 + w], 1u);
                     } else {
-                        w0 += f == 1u;
-                        w1 += f == 2u;
-                        w2 += f == 3u;
+                        if (in_bounds(g, f != 0u)) atomicAdd(&cnt[(3 + f) * 32 + w], 1u);
                         if (!claimed(u) && atomicCAS(posmap + u, -1, CLAIMED) == -1) {
                             const int32_t t = atomicAdd(&s_tcount, 1);
                             if (in_bounds(g, t < A.tcap)) {
@@ -343,17 +376,15 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         }
                     }
                 }
-                if (coop) {
-                    dh = warp_sum(dh);
-                    hc0 = warp_sum(hc0); hc1 = warp_sum(hc1); hc2 = warp_sum(hc2);
-                    w0 = warp_sum(w0); w1 = warp_sum(w1); w2 = warp_sum(w2);
+                __syncwarp();
+                if (i < L) {
+                    hptr[i] = (int32_t)cnt[lane];
+                    hcx[i * 3 + 0] = cnt[1 * 32 + lane]; hcx[i * 3 + 1] = cnt[2 * 32 + lane]; hcx[i * 3 + 2] = cnt[3 * 32 + lane];
+                    wx[i * 3 + 0] = cnt[4 * 32 + lane]; wx[i * 3 + 1] = cnt[5 * 32 + lane]; wx[i * 3 + 2] = cnt[6 * 32 + lane];
                 }
-                if (!coop || lane == 0) {
-                    hptr[i] = (int32_t)dh;
-                    hcx[i * 3 + 0] = hc0; hcx[i * 3 + 1] = hc1; hcx[i * 3 + 2] = hc2;
-                    wx[i * 3 + 0] = w0; wx[i * 3 + 1] = w1; wx[i * 3 + 2] = w2;
-                }
+                __syncwarp();
             }
+            for (int c = lane; c < C; c += 32) hv[c] = 0ull;
         }
         __syncthreads();
         const int32_t tcount = s_tcount;
@@ -371,51 +402,87 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
         }
 
         // ---- phase 3: H adjacency lists, H-edge types, per-Q-vertex P counts
-        for (int pass = 0; pass < 2; pass++) {
-            const bool coop = pass == 1;
-            for (int32_t i = coop ? warp : tid; i < L; i += coop ? HUB_WARPS : HUB_THREADS) {
-                const uint32_t ex = __ldg(P + i);
-                const uint32_t x = ex >> 2, fx = ex & 3u;
-                const int64_t xb = __ldg(g.rowptr + x), xe = __ldg(g.rowptr + x + 1);
-                if ((xe - xb > 32) != coop) continue;
-                const int64_t xu = upper_row(g.col, xb, xe, (uint32_t)r);
-                int32_t base = hptr[i];
-                uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
-                for (int64_t e0 = xu; e0 < xe; e0 += coop ? 32 : 1) {
-                    const int64_t e = e0 + (coop ? lane : 0);
-                    const bool valid = e < xe;
-                    const uint32_t ent = valid ? __ldg(g.col + e) : 0u;
+        // (chunks of members as in phase 2; H-lists in row = position order)
+        {
+            // [32] entries of NH(x) written so far, [9][32] NH(x) by (colour, flag)
+            uint32_t *srun = K == 4 ? reinterpret_cast<uint32_t *>(hv) : mscr[warp];
+            uint32_t *t9 = srun + 32;
+            for (;;) {
+                int32_t c0 = 0;
+                if (lane == 0) c0 = atomicAdd(&s_chunk3, psz);
+                c0 = __shfl_sync(0xffffffffu, c0, 0);
+                if (c0 >= L) break;
+                const int32_t i = lane < psz ? c0 + lane : L;
+                int64_t xe = 0;
+                int32_t len = 0, hb = 0;
+                uint32_t fx = 0u;
+                if (i < L) {
+                    const uint32_t ex = __ldg(P + i);
+                    const uint32_t x = ex >> 2;
+                    fx = ex & 3u;
+                    const int64_t xb = __ldg(g.rowptr + x);
+                    xe = __ldg(g.rowptr + x + 1);
+                    len = (int32_t)(xe - upper_row(g.col, xb, xe, (uint32_t)r));
+                    hb = hptr[i];
+                }
+                srun[lane] = 0u;
+#pragma unroll
+                for (int m = 0; m < 9; m++) t9[m * 32 + lane] = 0u;
+                int32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                for (int32_t base = 0; base < total; base += 32) {
+                    const int32_t jj = base + lane;
+                    int32_t w = 0;
+#pragma unroll
+                    for (int sh = 16; sh >= 1; sh >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= jj) w += sh;
+                    const int64_t xeo = __shfl_sync(0xffffffffu, xe, w);
+                    const int32_t io = __shfl_sync(0xffffffffu, incl, w);
+                    const int32_t hbo = __shfl_sync(0xffffffffu, hb, w);
+                    const uint32_t fxo = __shfl_sync(0xffffffffu, fx, w);
+                    const int32_t iown = __shfl_sync(0xffffffffu, i, w);
+                    const bool valid = jj < total;
+                    const uint32_t ent = valid ? __ldg(g.col + (xeo - (int64_t)(io - jj))) : 0u;
                     const uint32_t u = ent >> 2, f = ent & 3u;
                     const int32_t p = valid ? __ldcg(posmap + u) : -1;
                     const bool isH = valid && p >= 0;
-                    const uint32_t bal = coop ? __ballot_sync(0xffffffffu, isH) : (isH ? 1u : 0u);
-                    if (isH) {
-                        hlist[base + (coop ? __popc(bal & lt) : 0)] = ((uint32_t)p << 2) | f;
+                    // lanes of the same member in this window (idle lanes apart)
+                    const uint32_t grp = __match_any_sync(0xffffffffu, valid ? w : 32 + lane);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, isH) & grp;
+                    const uint32_t before = srun[w];
+                    if (isH && in_bounds(g, p < L && f != 0u)) {
+                        const int64_t idx = (int64_t)hbo + before + __popc(bal & lt);
+                        if (in_bounds(g, idx < A.hcap)) hlist[idx] = ((uint32_t)p << 2) | f;
                         const uint32_t cu = __ldg(P + p) & 3u;
-                        const uint32_t k9 = (cu - 1) * 3 + (f - 1);
-                        t0 += k9 == 0; t1 += k9 == 1; t2 += k9 == 2; t3 += k9 == 3; t4 += k9 == 4;
-                        t5 += k9 == 5; t6 += k9 == 6; t7 += k9 == 7; t8 += k9 == 8;
-                        if (i < p) hinc(hE, (uint32_t)etype(fx, cu, f));
-                    } else if (valid && p <= -3) {
+                        atomicAdd(&t9[((cu - 1) * 3 + (f - 1)) * 32 + w], 1u);
+                        if (iown < p) hinc(hE, (uint32_t)etype(fxo, cu, f));
+                    } else if (valid && p <= -3 && in_bounds(g, (-3 - (int64_t)p) < tcount && f != 0u)) {
                         const int64_t t = -3 - (int64_t)p;
-                        atomicAdd(qcnt + t * 9 + (fx - 1) * 3 + (f - 1), 1u);
+                        atomicAdd(qcnt + t * 9 + (fxo - 1) * 3 + (f - 1), 1u);
                     }
-                    base += __popc(bal);
+                    __syncwarp();
+                    if (valid && lane == __ffs(grp) - 1) srun[w] = before + __popc(bal);
+                    __syncwarp();
                 }
-                if (coop) {
-                    t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2); t3 = warp_sum(t3); t4 = warp_sum(t4);
-                    t5 = warp_sum(t5); t6 = warp_sum(t6); t7 = warp_sum(t7); t8 = warp_sum(t8);
-                }
-                if (!coop || lane == 0) {
+                if (i < L) {
+                    in_bounds(g, (int32_t)srun[lane] == hptr[i + 1] - hb);
                     uint32_t *h9 = htx + (int64_t)i * 9;
-                    h9[0] = t0; h9[1] = t1; h9[2] = t2; h9[3] = t3; h9[4] = t4;
-                    h9[5] = t5; h9[6] = t6; h9[7] = t7; h9[8] = t8;
+#pragma unroll
+                    for (int m = 0; m < 9; m++) h9[m] = t9[m * 32 + lane];
                     for (int f = 0; f < 3; f++) {
-                        const uint32_t w = wx[i * 3 + f];
-                        if (w) hadd(hW, (uint32_t)((fx - 1) * 3 + f), (unsigned long long)w);
+                        const uint32_t wv = wx[i * 3 + f];
+                        if (wv) hadd(hW, (uint32_t)((fx - 1) * 3 + f), (unsigned long long)wv);
                     }
                 }
+                __syncwarp();
             }
+            for (int c = lane; c < C; c += 32) hv[c] = 0ull;
         }
         __syncthreads();
 
