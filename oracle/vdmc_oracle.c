@@ -245,12 +245,45 @@ typedef struct {
     const int32_t *key;      /* order key per vertex (rank), or NULL for id */
     int32_t *roots;          /* vertices in the order they are taken as roots */
     int64_t nroots;
+    int64_t *eoff;           /* root i's initial extension set is eall[eoff[i], eoff[i+1]) */
+    int32_t *eall;
+    int32_t *troot;          /* per task t in [0, eoff[nroots]): its root index */
     uint64_t *out;
-    int64_t next;            /* shared root cursor */
+    int64_t next;            /* shared task cursor */
     int64_t found;           /* shared count of sets */
 } esu_job;
 
 static inline int32_t okey(const esu_job *J, int32_t v) { return J->key ? J->key[v] : v; }
+
+static int64_t esu_extend(const esu_job *J, int32_t *sub, int nsub, const int32_t *ext, int next, int32_t root);
+
+/*
+ * One step of ESU: add w to V_sub, whose remaining extension set is
+ * rem[0, nrem), and recurse with
+ *   V'_ext = rem  U  { u in N_excl(w, V_sub) : u > root }.
+ */
+static int64_t esu_take(const esu_job *J, int32_t *sub, int nsub, const int32_t *rem, int nrem, int32_t w,
+                        int32_t root) {
+    int32_t cur[4096];
+    int64_t deg = J->g->uptr[w + 1] - J->g->uptr[w];
+    int64_t cap = nrem + deg;
+    int32_t *heap_buf = cap <= 4096 ? NULL : malloc(sizeof(int32_t) * (size_t)cap);
+    int32_t *ne = heap_buf ? heap_buf : cur;
+    int nn = 0;
+    for (int i = 0; i < nrem; i++) ne[nn++] = rem[i];
+    for (int64_t e = J->g->uptr[w]; e < J->g->uptr[w + 1]; e++) {
+        int32_t u = J->g->uadj[e];
+        if (okey(J, u) <= okey(J, root)) continue;
+        int excl = 1;
+        for (int s = 0; s < nsub && excl; s++)
+            if (u == sub[s] || u_adjacent(J->g, u, sub[s])) excl = 0;
+        if (excl) ne[nn++] = u;
+    }
+    sub[nsub] = w;
+    int64_t found = esu_extend(J, sub, nsub + 1, ne, nn, root);
+    free(heap_buf);
+    return found;
+}
 
 static int64_t esu_extend(const esu_job *J, int32_t *sub, int nsub, const int32_t *ext, int next, int32_t root) {
     if (nsub == J->k) {
@@ -258,51 +291,31 @@ static int64_t esu_extend(const esu_job *J, int32_t *sub, int nsub, const int32_
         return 1;
     }
     int64_t found = 0;
-    /* V_ext is consumed one element w at a time */
-    int32_t cur[4096];
-    int32_t *rem = (int32_t *)ext;
-    int nrem = next;
-    int32_t *heap_buf = NULL;
-    while (nrem > 0) {
-        int32_t w = rem[--nrem];
-        /* V'_ext = remaining V_ext  U  { u in N_excl(w, V_sub) : u > root } */
-        int64_t deg = J->g->uptr[w + 1] - J->g->uptr[w];
-        int64_t cap = nrem + deg;
-        int32_t *ne = cap <= 4096 ? cur : (heap_buf = realloc(heap_buf, sizeof(int32_t) * (size_t)cap));
-        int nn = 0;
-        for (int i = 0; i < nrem; i++) ne[nn++] = rem[i];
-        for (int64_t e = J->g->uptr[w]; e < J->g->uptr[w + 1]; e++) {
-            int32_t u = J->g->uadj[e];
-            if (okey(J, u) <= okey(J, root)) continue;
-            int excl = 1;
-            for (int s = 0; s < nsub && excl; s++)
-                if (u == sub[s] || u_adjacent(J->g, u, sub[s])) excl = 0;
-            if (excl) ne[nn++] = u;
-        }
-        sub[nsub] = w;
-        found += esu_extend(J, sub, nsub + 1, ne, nn, root);
-    }
-    free(heap_buf);
+    /* V_ext is consumed one element w at a time, from its end */
+    for (int nrem = next - 1; nrem >= 0; nrem--) found += esu_take(J, sub, nsub, ext, nrem, ext[nrem], root);
     return found;
 }
 
+/*
+ * Threads take tasks (root v, j): the sub-tree of ESU in which the first
+ * vertex added to {v} is the j-th element of v's initial extension set
+ * (elements j+1, ... having been consumed already).  These sub-trees
+ * partition v's sets, so one heavy root is shared among threads.
+ */
 static void *esu_worker(void *arg) {
     esu_job *J = (esu_job *)arg;
     int64_t local = 0;
     int32_t sub[MAXK];
+    const int64_t ntasks = J->eoff[J->nroots];
     for (;;) {
-        int64_t i = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
-        if (i >= J->nroots) break;
-        int32_t v = J->roots[i];
-        const ograph *g = J->g;
-        int64_t deg = g->uptr[v + 1] - g->uptr[v];
-        int32_t *ext = malloc(sizeof(int32_t) * (size_t)(deg > 0 ? deg : 1));
-        int ne = 0;
-        for (int64_t e = g->uptr[v]; e < g->uptr[v + 1]; e++)
-            if (okey(J, g->uadj[e]) > okey(J, v)) ext[ne++] = g->uadj[e];
+        int64_t t = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (t >= ntasks) break;
+        const int64_t i = J->troot[t];
+        const int32_t v = J->roots[i];
+        const int32_t *ext = J->eall + J->eoff[i];
+        const int j = (int)(t - J->eoff[i]);
         sub[0] = v;
-        local += esu_extend(J, sub, 1, ext, ne, v);
-        free(ext);
+        local += esu_take(J, sub, 1, ext, j, ext[j], v);
     }
     __atomic_fetch_add(&J->found, local, __ATOMIC_RELAXED);
     return NULL;
@@ -337,12 +350,36 @@ int64_t oracle_count_esu(int32_t n, int64_t m, const int32_t *src, const int32_t
     J.roots = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int32_t v = 0; v < n; v++)
         if (!key || (key[v] >= key_lo && key[v] < key_hi)) J.roots[J.nroots++] = v;
+    /* initial extension sets: the neighbours of each root with a larger key */
+    J.eoff = malloc(sizeof(int64_t) * (size_t)(J.nroots + 1));
+    J.eoff[0] = 0;
+    for (int64_t i = 0; i < J.nroots; i++) {
+        const int32_t v = J.roots[i];
+        int64_t c = 0;
+        for (int64_t e = g.uptr[v]; e < g.uptr[v + 1]; e++) c += okey(&J, g.uadj[e]) > okey(&J, v);
+        J.eoff[i + 1] = J.eoff[i] + c;
+    }
+    const int64_t ntasks = J.eoff[J.nroots];
+    J.eall = malloc(sizeof(int32_t) * (size_t)(ntasks > 0 ? ntasks : 1));
+    J.troot = malloc(sizeof(int32_t) * (size_t)(ntasks > 0 ? ntasks : 1));
+    for (int64_t i = 0; i < J.nroots; i++) {
+        const int32_t v = J.roots[i];
+        int64_t o = J.eoff[i];
+        for (int64_t e = g.uptr[v]; e < g.uptr[v + 1]; e++)
+            if (okey(&J, g.uadj[e]) > okey(&J, v)) {
+                J.eall[o] = g.uadj[e];
+                J.troot[o++] = (int32_t)i;
+            }
+    }
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];
     for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, esu_worker, &J);
     for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     free(J.roots);
+    free(J.eoff);
+    free(J.eall);
+    free(J.troot);
     ograph_free(&g);
     return J.found;
 }
