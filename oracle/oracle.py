@@ -47,6 +47,9 @@ def _load():
         lib.oracle_count_esu.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int,
                                          i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, u64p]
         lib.oracle_count_esu.restype = ctypes.c_int64
+        lib.oracle_count_esu_masked.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int, i32p,
+                                                ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, u64p]
+        lib.oracle_count_esu_masked.restype = ctypes.c_int64
         lib.oracle_count_brute.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int, u64p]
         lib.oracle_count_brute.restype = ctypes.c_int64
         lib.oracle_degree_rank.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p]
@@ -128,6 +131,25 @@ def count_roots(n, src, dst, k, rank, lo, hi, threads: int | None = None):
                                threads or default_threads(), _ptr(out, ctypes.c_uint64))
     if got < 0:
         raise ValueError("oracle_count_esu failed (%d)" % got)
+    return out, int(got)
+
+
+def count_root_ranges(n, src, dst, k, rank, ranges, threads: int | None = None):
+    """Counts over the connected k-sets whose lowest-rank member has rank in any of
+    the disjoint ``ranges`` [(lo, hi), ...] (one graph build for all of them)."""
+    lib = _load()
+    src, dst = _i32(src), _i32(dst)
+    rank = _i32(rank)
+    mask = np.zeros(n, np.uint8)
+    for lo, hi in ranges:
+        mask[(rank >= lo) & (rank < hi)] = 1
+    nc = num_classes(k)
+    out = np.zeros((n, nc), np.uint64)
+    got = lib.oracle_count_esu_masked(n, src.size, _ptr(src, ctypes.c_int32), _ptr(dst, ctypes.c_int32), k,
+                                      _ptr(rank, ctypes.c_int32), _ptr(mask, ctypes.c_uint8),
+                                      threads or default_threads(), _ptr(out, ctypes.c_uint64))
+    if got < 0:
+        raise ValueError("oracle_count_esu_masked failed (%d)" % got)
     return out, int(got)
 
 

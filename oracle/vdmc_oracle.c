@@ -264,6 +264,11 @@ static int64_t esu_extend(const esu_job *J, int32_t *sub, int nsub, const int32_
  */
 static int64_t esu_take(const esu_job *J, int32_t *sub, int nsub, const int32_t *rem, int nrem, int32_t w,
                         int32_t root) {
+    if (nsub + 1 == J->k) {  /* w completes the set: V'_ext would never be used */
+        sub[nsub] = w;
+        credit_set(J->g, J->cl, J->k, sub, J->out);
+        return 1;
+    }
     int32_t cur[4096];
     int64_t deg = J->g->uptr[w + 1] - J->g->uptr[w];
     int64_t cap = nrem + deg;
@@ -333,9 +338,30 @@ static int load_classes(int k, oclasses *cl) {
  * key == NULL the key is the vertex id and every set is counted
  * (key_lo/key_hi ignored).  Returns the number of sets, or < 0 on error.
  */
+static int64_t count_esu_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
+                              const int32_t *key, int32_t key_lo, int32_t key_hi, const uint8_t *root_mask,
+                              int nthreads, uint64_t *out);
+
 int64_t oracle_count_esu(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
                          const int32_t *key, int32_t key_lo, int32_t key_hi, int nthreads,
                          uint64_t *out) {
+    return count_esu_impl(n, m, src, dst, k, key, key_lo, key_hi, NULL, nthreads, out);
+}
+
+/*
+ * As oracle_count_esu with a key, but the roots are the vertices v with
+ * root_mask[v] != 0 (any set of keys, e.g. several key ranges at once):
+ * counts over the connected k-sets whose minimum-key vertex is such a root.
+ */
+int64_t oracle_count_esu_masked(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
+                                const int32_t *key, const uint8_t *root_mask, int nthreads, uint64_t *out) {
+    if (!key || !root_mask) return -1;
+    return count_esu_impl(n, m, src, dst, k, key, 0, 0, root_mask, nthreads, out);
+}
+
+static int64_t count_esu_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
+                              const int32_t *key, int32_t key_lo, int32_t key_hi, const uint8_t *root_mask,
+                              int nthreads, uint64_t *out) {
     if (k != 3 && k != 4) return -1;
     if (n < 0 || m < 0) return -1;
     oclasses cl;
@@ -349,7 +375,7 @@ int64_t oracle_count_esu(int32_t n, int64_t m, const int32_t *src, const int32_t
     J.g = &g; J.cl = &cl; J.k = k; J.key = key; J.out = out;
     J.roots = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int32_t v = 0; v < n; v++)
-        if (!key || (key[v] >= key_lo && key[v] < key_hi)) J.roots[J.nroots++] = v;
+        if (!key || (root_mask ? root_mask[v] != 0 : (key[v] >= key_lo && key[v] < key_hi))) J.roots[J.nroots++] = v;
     /* initial extension sets: the neighbours of each root with a larger key */
     J.eoff = malloc(sizeof(int64_t) * (size_t)(J.nroots + 1));
     J.eoff[0] = 0;

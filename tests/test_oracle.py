@@ -316,6 +316,17 @@ def test_root_ranges_partition_the_count():
             tot += g
         assert tot == gf
         np.testing.assert_array_equal(acc, full)
+        # several ranges in one call == the sum of the single-range calls
+        ranges = ((0, 5), (40, 41), (100, 160))
+        multi, gm = O.count_root_ranges(n, s, d, k, rank, ranges)
+        acc = np.zeros_like(full)
+        tot = 0
+        for lo, hi in ranges:
+            part, g = O.count_roots(n, s, d, k, rank, lo, hi)
+            acc += part
+            tot += g
+        assert gm == tot
+        np.testing.assert_array_equal(multi, acc)
 
 
 # ------------------------------------------------------- G(n,p), Eq. 4 --
