@@ -50,6 +50,14 @@ def _load():
         lib.oracle_count_esu_masked.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int, i32p,
                                                 ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, u64p]
         lib.oracle_count_esu_masked.restype = ctypes.c_int64
+        lib.oracle_classes_undirected.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint16),
+                                                  ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        lib.oracle_classes_undirected.restype = ctypes.c_int
+        lib.oracle_count_mode.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, u64p]
+        lib.oracle_count_mode.restype = ctypes.c_int64
+        lib.oracle_edges.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i32p]
+        lib.oracle_edges.restype = ctypes.c_int64
         lib.oracle_count_brute.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, ctypes.c_int, u64p]
         lib.oracle_count_brute.restype = ctypes.c_int64
         lib.oracle_degree_rank.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p]
@@ -153,6 +161,61 @@ def count_root_ranges(n, src, dst, k, rank, ranges, threads: int | None = None):
     return out, int(got)
 
 
+def classes_undirected(k: int):
+    """Undirected connected classes: (minimum symmetric indices ascending, labelled graphs per class)."""
+    lib = _load()
+    cap = 64
+    canon = np.zeros(cap, np.uint16)
+    niso = np.zeros(cap, np.uint32)
+    nc = lib.oracle_classes_undirected(k, _ptr(canon, ctypes.c_uint16), _ptr(niso, ctypes.c_uint32), cap)
+    if nc < 0:
+        raise ValueError("k must be 2..4")
+    return canon[:nc].astype(np.int64), niso[:nc].astype(np.int64)
+
+
+def edges(n, src, dst):
+    """Edges {u, v} of G_U, u < v, in (u, v) order: the rows of per-edge counts. Returns (u, v)."""
+    lib = _load()
+    src, dst = _i32(src), _i32(dst)
+    ne = lib.oracle_edges(n, src.size, _ptr(src, ctypes.c_int32), _ptr(dst, ctypes.c_int32), None, None)
+    if ne < 0:
+        raise ValueError("oracle_edges failed (%d)" % ne)
+    u = np.zeros(ne, np.int32)
+    v = np.zeros(ne, np.int32)
+    lib.oracle_edges(n, src.size, _ptr(src, ctypes.c_int32), _ptr(dst, ctypes.c_int32), _ptr(u, ctypes.c_int32),
+                     _ptr(v, ctypes.c_int32))
+    return u, v
+
+
+def count_mode(n, src, dst, k, undirected=False, per_edge=False, rank=None, ranges=None,
+               threads: int | None = None):
+    """Counts of the undirected and/or per-edge variants.
+
+    Rows: vertices, or the edges of G_U in the order of :func:`edges` when
+    per_edge; columns: the directed classes, or :func:`classes_undirected`
+    when undirected.  With rank and ranges: only the sets whose lowest-rank
+    member has rank in one of the ranges.  Returns (counts, number_of_sets)."""
+    lib = _load()
+    src, dst = _i32(src), _i32(dst)
+    nc = len(classes_undirected(k)[0]) if undirected else num_classes(k)
+    rows = len(edges(n, src, dst)[0]) if per_edge else n
+    out = np.zeros((rows, nc), np.uint64)
+    key = mask = None
+    if ranges is not None:
+        key = _i32(rank)
+        m8 = np.zeros(n, np.uint8)
+        for lo, hi in ranges:
+            m8[(key >= lo) & (key < hi)] = 1
+        mask = _ptr(m8, ctypes.c_uint8)
+    got = lib.oracle_count_mode(n, src.size, _ptr(src, ctypes.c_int32), _ptr(dst, ctypes.c_int32), k,
+                                1 if undirected else 0, 1 if per_edge else 0,
+                                _ptr(key, ctypes.c_int32) if key is not None else None, mask,
+                                threads or default_threads(), _ptr(out, ctypes.c_uint64))
+    if got < 0:
+        raise ValueError("oracle_count_mode failed (%d)" % got)
+    return out, int(got)
+
+
 def count_brute(n, src, dst, k):
     """Per-vertex counts by brute force over all C(n, k) vertex subsets."""
     lib = _load()
@@ -171,12 +234,14 @@ def motif_edges(k: int, idx: int) -> int:
     return bin(int(idx)).count("1")
 
 
-def gnp_expected_local(n: int, p: float, k: int):
+def gnp_expected_local(n: int, p: float, k: int, undirected: bool = False):
     """Eq. 4: E[X_{k,m}(i)] = C(n-1, k-1) * N_Iso(m) * p^{n_e} * (1-p)^{n_max - n_e}.
 
-    n_max(k) = k(k-1) for directed graphs (the text after Eq. 4's
-    definitions).  Returns a float64 array over the connected classes."""
-    canon, niso = classes(k)
-    nmax = k * (k - 1)
-    ne = np.array([motif_edges(k, c) for c in canon], dtype=np.float64)
+    n_max(k) = k(k-1) for directed graphs and C(k, 2) for undirected ones
+    (the text after Eq. 4's definitions); for an undirected motif n_e is its
+    number of edges, half the set bits of its symmetric index.  Returns a
+    float64 array over the connected classes."""
+    canon, niso = classes_undirected(k) if undirected else classes(k)
+    nmax = k * (k - 1) // 2 if undirected else k * (k - 1)
+    ne = np.array([motif_edges(k, c) for c in canon], dtype=np.float64) / (2.0 if undirected else 1.0)
     return math.comb(n - 1, k - 1) * niso * (p ** ne) * ((1 - p) ** (nmax - ne))

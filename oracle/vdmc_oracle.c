@@ -133,6 +133,41 @@ int oracle_classes(int k, int connected_only, uint16_t *canon, uint32_t *niso, i
     return nc;
 }
 
+/*
+ * Undirected variant (the undirected motifs of Tables 1-2 and Fig. 5): the
+ * classes of connected simple undirected graphs on k vertices, each named
+ * by the minimum index of its (symmetric) adjacency matrix under the same
+ * bit order; niso[c] = labelled graphs in class c.  Returns the number of
+ * classes, or -1.
+ */
+int oracle_classes_undirected(int k, uint16_t *canon, uint32_t *niso, int cap) {
+    if (k < 2 || k > MAXK) return -1;
+    int nidx = 1 << (k * (k - 1));
+    int *cnt = calloc((size_t)nidx, sizeof(int));
+    if (!cnt) return -1;
+    int adj[MAXK * MAXK];
+    for (int idx = 0; idx < nidx; idx++) {
+        index_to_matrix(k, idx, adj);
+        int sym = 1;
+        for (int i = 0; i < k && sym; i++)
+            for (int j = 0; j < k; j++)
+                if (adj[i * k + j] != adj[j * k + i]) { sym = 0; break; }
+        if (!sym || !index_is_connected(k, idx)) continue;
+        cnt[oracle_canonical_index(k, idx)]++;
+    }
+    int nc = 0;
+    for (int idx = 0; idx < nidx; idx++)
+        if (cnt[idx]) {
+            if (nc < cap) {
+                if (canon) canon[nc] = (uint16_t)idx;
+                if (niso) niso[nc] = (uint32_t)cnt[idx];
+            }
+            nc++;
+        }
+    free(cnt);
+    return nc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Graph as plain sorted adjacency lists in ORIGINAL ids.              */
 /* ------------------------------------------------------------------ */
@@ -141,6 +176,8 @@ typedef struct {
     int32_t n;
     int64_t *optr; int32_t *oadj;   /* out-arcs, sorted, distinct */
     int64_t *uptr; int32_t *uadj;   /* G_U neighbours, sorted, distinct */
+    int64_t *eup;                   /* per vertex u: first position in uadj of a neighbour > u */
+    int64_t *erow;                  /* per vertex u: edges {u', v'}, u' < v', with u' < u */
 } ograph;
 
 static int cmp_i64(const void *a, const void *b) {
@@ -149,7 +186,7 @@ static int cmp_i64(const void *a, const void *b) {
 }
 
 static void ograph_free(ograph *g) {
-    free(g->optr); free(g->oadj); free(g->uptr); free(g->uadj);
+    free(g->optr); free(g->oadj); free(g->uptr); free(g->uadj); free(g->eup); free(g->erow);
     memset(g, 0, sizeof *g);
 }
 
@@ -185,7 +222,29 @@ static int ograph_build(ograph *g, int32_t n, int64_t m, const int32_t *src, con
     for (int64_t i = 0; i < mu; i++) { g->uptr[ukey[i] / n + 1]++; g->uadj[i] = (int32_t)(ukey[i] % n); }
     for (int32_t v = 0; v < n; v++) { g->optr[v + 1] += g->optr[v]; g->uptr[v + 1] += g->uptr[v]; }
     free(key); free(ukey);
+    /* rows of the per-edge output: edges {u, v}, u < v, in (u, v) order */
+    g->eup = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    g->erow = malloc(sizeof(int64_t) * ((size_t)n + 1));
+    if (!g->eup || !g->erow) { ograph_free(g); return -1; }
+    g->erow[0] = 0;
+    for (int32_t u = 0; u < n; u++) {
+        int64_t e = g->uptr[u];
+        while (e < g->uptr[u + 1] && g->uadj[e] < u) e++;
+        g->eup[u] = e;
+        g->erow[u + 1] = g->erow[u] + (g->uptr[u + 1] - e);
+    }
     return 0;
+}
+
+/* output row of the edge {u, v} of G_U (which must exist) */
+static int64_t edge_row(const ograph *g, int32_t u, int32_t v) {
+    if (u > v) { int32_t t = u; u = v; v = t; }
+    int64_t lo = g->eup[u], hi = g->uptr[u + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (g->uadj[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return g->erow[u] + (lo - g->eup[u]);
 }
 
 static int has_arc(const ograph *g, int32_t u, int32_t v) {
@@ -208,7 +267,13 @@ static int u_adjacent(const ograph *g, int32_t u, int32_t v) {
 }
 
 /* Sorted connected-class list of the oracle itself, for the column lookup. */
-typedef struct { int k, nc; uint16_t canon[256]; } oclasses;
+/* The class list in use and what is credited:
+ *   undirected = 0: directed motifs (entry (i,j) = arc i -> j)
+ *   undirected = 1: undirected motifs of G_U (entry (i,j) = edge {i,j})
+ *   per_edge   = 0: each member vertex gets +1 (X_{k,m}(i))
+ *   per_edge   = 1: each edge of G_U inside the set gets +1 instead (the
+ *                   edge variant of the Discussion) */
+typedef struct { int k, nc, undirected, per_edge; uint16_t canon[256]; } oclasses;
 
 static int class_column(const oclasses *c, int canon_idx) {
     int lo = 0, hi = c->nc - 1;
@@ -225,11 +290,19 @@ static void credit_set(const ograph *g, const oclasses *cl, int k, const int32_t
     int adj[MAXK * MAXK];
     for (int i = 0; i < k; i++)
         for (int j = 0; j < k; j++)
-            adj[i * k + j] = (i != j) && has_arc(g, S[i], S[j]);
+            adj[i * k + j] = (i != j) && (cl->undirected ? u_adjacent(g, S[i], S[j]) : has_arc(g, S[i], S[j]));
     int idx = matrix_to_index(k, adj);
     int col = class_column(cl, oracle_canonical_index(k, idx));
+    if (!cl->per_edge) {
+        for (int i = 0; i < k; i++)
+            __atomic_fetch_add(&out[(size_t)S[i] * (size_t)cl->nc + (size_t)col], (uint64_t)1, __ATOMIC_RELAXED);
+        return;
+    }
     for (int i = 0; i < k; i++)
-        __atomic_fetch_add(&out[(size_t)S[i] * (size_t)cl->nc + (size_t)col], (uint64_t)1, __ATOMIC_RELAXED);
+        for (int j = i + 1; j < k; j++)
+            if (u_adjacent(g, S[i], S[j]))
+                __atomic_fetch_add(&out[(size_t)edge_row(g, S[i], S[j]) * (size_t)cl->nc + (size_t)col], (uint64_t)1,
+                                   __ATOMIC_RELAXED);
 }
 
 /* ------------------------------------------------------------------ */
@@ -326,11 +399,15 @@ static void *esu_worker(void *arg) {
     return NULL;
 }
 
-static int load_classes(int k, oclasses *cl) {
+static int load_classes_mode(int k, int undirected, int per_edge, oclasses *cl) {
     cl->k = k;
-    cl->nc = oracle_classes(k, 1, cl->canon, NULL, 256);
+    cl->undirected = undirected;
+    cl->per_edge = per_edge;
+    cl->nc = undirected ? oracle_classes_undirected(k, cl->canon, NULL, 256) : oracle_classes(k, 1, cl->canon, NULL, 256);
     return cl->nc > 0 ? 0 : -1;
 }
+
+static int load_classes(int k, oclasses *cl) { return load_classes_mode(k, 0, 0, cl); }
 
 /*
  * Per-vertex counts out[v * C_k + c] (overwritten) over all connected
@@ -339,13 +416,44 @@ static int load_classes(int k, oclasses *cl) {
  * (key_lo/key_hi ignored).  Returns the number of sets, or < 0 on error.
  */
 static int64_t count_esu_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
-                              const int32_t *key, int32_t key_lo, int32_t key_hi, const uint8_t *root_mask,
-                              int nthreads, uint64_t *out);
+                              int undirected, int per_edge, const int32_t *key, int32_t key_lo, int32_t key_hi,
+                              const uint8_t *root_mask, int nthreads, uint64_t *out);
 
 int64_t oracle_count_esu(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
                          const int32_t *key, int32_t key_lo, int32_t key_hi, int nthreads,
                          uint64_t *out) {
-    return count_esu_impl(n, m, src, dst, k, key, key_lo, key_hi, NULL, nthreads, out);
+    return count_esu_impl(n, m, src, dst, k, 0, 0, key, key_lo, key_hi, NULL, nthreads, out);
+}
+
+/*
+ * The undirected and per-edge variants (and both): `out` has n rows
+ * (per_edge = 0) or one row per edge of G_U (per_edge = 1, rows in the
+ * order of oracle_edges), and C columns of the class list of the mode
+ * (oracle_classes or oracle_classes_undirected).  root_mask as in
+ * oracle_count_esu_masked (with key), or NULL for every root.
+ */
+int64_t oracle_count_mode(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k, int undirected,
+                          int per_edge, const int32_t *key, const uint8_t *root_mask, int nthreads, uint64_t *out) {
+    if (root_mask && !key) return -1;
+    return count_esu_impl(n, m, src, dst, k, undirected ? 1 : 0, per_edge ? 1 : 0, key, 0, 0, root_mask, nthreads,
+                          out);
+}
+
+/* Edges {u, v} of G_U with u < v (original ids) in (u, v) order: the rows of
+ * the per-edge output.  Fills u_out/v_out when not NULL; returns the count. */
+int64_t oracle_edges(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int32_t *u_out, int32_t *v_out) {
+    ograph g;
+    int rc = ograph_build(&g, n, m, src, dst);
+    if (rc) return rc;
+    const int64_t ne = g.erow[n];
+    for (int32_t u = 0; u < n; u++)
+        for (int64_t e = g.eup[u]; e < g.uptr[u + 1]; e++) {
+            const int64_t row = g.erow[u] + (e - g.eup[u]);
+            if (u_out) u_out[row] = u;
+            if (v_out) v_out[row] = g.uadj[e];
+        }
+    ograph_free(&g);
+    return ne;
 }
 
 /*
@@ -356,20 +464,21 @@ int64_t oracle_count_esu(int32_t n, int64_t m, const int32_t *src, const int32_t
 int64_t oracle_count_esu_masked(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
                                 const int32_t *key, const uint8_t *root_mask, int nthreads, uint64_t *out) {
     if (!key || !root_mask) return -1;
-    return count_esu_impl(n, m, src, dst, k, key, 0, 0, root_mask, nthreads, out);
+    return count_esu_impl(n, m, src, dst, k, 0, 0, key, 0, 0, root_mask, nthreads, out);
 }
 
 static int64_t count_esu_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int k,
-                              const int32_t *key, int32_t key_lo, int32_t key_hi, const uint8_t *root_mask,
-                              int nthreads, uint64_t *out) {
+                              int undirected, int per_edge, const int32_t *key, int32_t key_lo, int32_t key_hi,
+                              const uint8_t *root_mask, int nthreads, uint64_t *out) {
     if (k != 3 && k != 4) return -1;
     if (n < 0 || m < 0) return -1;
     oclasses cl;
-    if (load_classes(k, &cl)) return -1;
-    memset(out, 0, sizeof(uint64_t) * (size_t)n * (size_t)cl.nc);
+    if (load_classes_mode(k, undirected, per_edge, &cl)) return -1;
     ograph g;
     int rc = ograph_build(&g, n, m, src, dst);
     if (rc) return rc == -2 ? -2 : -1;
+    const size_t rows = per_edge ? (size_t)g.erow[n] : (size_t)n;
+    memset(out, 0, sizeof(uint64_t) * rows * (size_t)cl.nc);
     esu_job J;
     memset(&J, 0, sizeof J);
     J.g = &g; J.cl = &cl; J.k = k; J.key = key; J.out = out;

@@ -14,6 +14,8 @@ Workload shapes:
 * ``gnp``       -- directed G(n, p): every ordered pair (i, j), i != j, is an
                    arc independently with probability p (the random-graph
                    model of the section comparing VDMC to theory in G(n,p)).
+* ``gnp_undirected`` -- undirected G(n, p): every unordered pair is an edge
+                   with probability p, given as one arc i -> j, i < j.
 * ``chung_lu``  -- directed Chung-Lu graph with Pareto out- and in-weights
                    (fat-tailed degree, the shape of the real networks of
                    Table 1), optional reciprocity.
@@ -32,6 +34,7 @@ import numpy as np
 
 __all__ = [
     "gnp",
+    "gnp_undirected",
     "chung_lu",
     "er_uniform",
     "batch",
@@ -81,6 +84,14 @@ def gnp(n: int, p: float, seed: int):
     j = j + (j >= i)
     src, dst = simple_arcs(i, j)
     return n, src, dst
+
+
+def gnp_undirected(n: int, p: float, seed: int):
+    """Undirected G(n, p): each unordered pair {i, j} is an edge with probability p (one arc i -> j, i < j)."""
+    rng = _rng(seed)
+    a = np.triu(rng.random((n, n)) < p, k=1)
+    src, dst = np.nonzero(a)
+    return n, src.astype(np.int32), dst.astype(np.int32)
 
 
 def _draw_weighted(rng, w, size):

@@ -359,3 +359,201 @@ def test_gnp_expectation_eq4(k, seeds):
     sets_obs = tot_obs / k
     sets_exp = tot_exp / k
     assert np.all(sets_obs <= sets_exp + 8 * np.sqrt(sets_exp) + 12)
+
+
+# ----------------------------------------- undirected and per-edge modes --
+# The undirected motifs of Tables 1-2 / Fig. 5 and the per-edge counts of the
+# Discussion, pinned by an independent brute force written here in Python
+# (its own class list, its own connectivity test), closed forms, the
+# undirected form of Eq. 4 and counting identities.
+
+import itertools
+
+
+def _py_index(k, adj):
+    idx = 0
+    for i in range(k):
+        for j in range(k):
+            if i != j:
+                idx = (idx << 1) | int(adj[i][j])
+    return idx
+
+
+def _py_canon(k, adj):
+    return min(_py_index(k, [[adj[p[i]][p[j]] for j in range(k)] for i in range(k)])
+               for p in itertools.permutations(range(k)))
+
+
+def _py_classes(k, undirected):
+    out = set()
+    nb = k * (k - 1)
+    for idx in range(1 << nb):
+        adj = [[0] * k for _ in range(k)]
+        b = nb - 1
+        for i in range(k):
+            for j in range(k):
+                if i != j:
+                    adj[i][j] = (idx >> b) & 1
+                    b -= 1
+        if undirected and any(adj[i][j] != adj[j][i] for i in range(k) for j in range(k)):
+            continue
+        und = [[adj[i][j] or adj[j][i] for j in range(k)] for i in range(k)]
+        seen, stack = {0}, [0]
+        while stack:
+            x = stack.pop()
+            for y in range(k):
+                if und[x][y] and y not in seen:
+                    seen.add(y)
+                    stack.append(y)
+        if len(seen) == k:
+            out.add(_py_canon(k, adj))
+    return sorted(out)
+
+
+def _py_brute(n, s, d, k, undirected, per_edge):
+    arcs = set(zip(s.tolist(), d.tolist())) - {(x, x) for x in range(n)}
+    und = {(a, b) for a, b in arcs} | {(b, a) for a, b in arcs}
+    cls = _py_classes(k, undirected)
+    col = {m: i for i, m in enumerate(cls)}
+    edges = sorted({(min(a, b), max(a, b)) for a, b in arcs})
+    erow = {e: i for i, e in enumerate(edges)}
+    out = np.zeros((len(edges) if per_edge else n, len(cls)), np.uint64)
+    for S in itertools.combinations(range(n), k):
+        seen, stack = {S[0]}, [S[0]]
+        while stack:
+            x = stack.pop()
+            for y in S:
+                if (x, y) in und and y not in seen:
+                    seen.add(y)
+                    stack.append(y)
+        if len(seen) < k:
+            continue
+        rel = und if undirected else arcs
+        adj = [[int(i != j and (S[i], S[j]) in rel) for j in range(k)] for i in range(k)]
+        c = col[_py_canon(k, adj)]
+        if per_edge:
+            for i in range(k):
+                for j in range(i + 1, k):
+                    if (S[i], S[j]) in und:
+                        out[erow[(S[i], S[j])], c] += 1
+        else:
+            for v in S:
+                out[v, c] += 1
+    return out
+
+
+def test_undirected_class_counts():
+    # connected graphs on 3 and 4 vertices: 2 and 6 (OEIS A001349); labelled
+    # connected graphs: 4 and 38 (A001187)
+    for k, nc, lab in ((3, 2, 4), (4, 6, 38)):
+        canon, niso = O.classes_undirected(k)
+        assert len(canon) == nc and int(niso.sum()) == lab
+        assert canon.tolist() == _py_classes(k, True)
+        # each undirected class is the directed class of its symmetric matrix
+        assert set(canon.tolist()) <= set(O.classes(k)[0].tolist())
+    assert O.classes(3)[0].tolist() == _py_classes(3, False)
+
+
+@pytest.mark.parametrize("undirected,per_edge", [(True, False), (False, True), (True, True)])
+def test_modes_match_python_brute_force(undirected, per_edge):
+    rng = np.random.default_rng(7)
+    for trial in range(14):
+        n = int(rng.integers(4, 11))
+        p = float(rng.uniform(0.15, 0.5))
+        n, s, d = synth.gnp(n, p, 500 + trial)
+        for k in (3, 4):
+            want = _py_brute(n, s, d, k, undirected, per_edge)
+            got, found = O.count_mode(n, s, d, k, undirected=undirected, per_edge=per_edge)
+            np.testing.assert_array_equal(got, want, err_msg="trial %d k=%d" % (trial, k))
+
+
+def _undirected_arcs(pairs):
+    return (np.array([a for a, b in pairs], np.int32), np.array([b for a, b in pairs], np.int32))
+
+
+def test_undirected_and_per_edge_closed_forms():
+    cu3, cu4 = O.classes_undirected(3)[0].tolist(), O.classes_undirected(4)[0].tolist()
+    tri, k4 = cu3.index(63), cu4.index(4095)
+    path3 = cu3.index(23)
+    # complete graph K_n (one arc per pair): every vertex in C(n-1,2) triangles / C(n-1,3) K4s
+    for n in (5, 7):
+        s, d = _undirected_arcs([(i, j) for i in range(n) for j in range(i + 1, n)])
+        x3, _ = O.count_mode(n, s, d, 3, undirected=True)
+        x4, _ = O.count_mode(n, s, d, 4, undirected=True)
+        assert (x3[:, tri] == math.comb(n - 1, 2)).all() and x3.sum() == n * math.comb(n - 1, 2)
+        assert (x4[:, k4] == math.comb(n - 1, 3)).all() and x4.sum() == n * math.comb(n - 1, 3)
+        e3, _ = O.count_mode(n, s, d, 3, undirected=True, per_edge=True)
+        e4, _ = O.count_mode(n, s, d, 4, undirected=True, per_edge=True)
+        assert (e3[:, tri] == n - 2).all() and (e4[:, k4] == math.comb(n - 2, 2)).all()
+    # star with L leaves: paths centre C(L,2), leaf L-1; 3-stars centre C(L,3), leaf C(L-1,2)
+    L = 6
+    s, d = _undirected_arcs([(0, i) for i in range(1, L + 1)])
+    x3, _ = O.count_mode(L + 1, s, d, 3, undirected=True)
+    assert x3[0, path3] == math.comb(L, 2) and (x3[1:, path3] == L - 1).all()
+    x4, _ = O.count_mode(L + 1, s, d, 4, undirected=True)
+    star = int(np.nonzero(x4[0])[0][0])
+    assert x4[0, star] == math.comb(L, 3) and (x4[1:, star] == math.comb(L - 1, 2)).all()
+    assert O.classes_undirected(4)[1][star] == 4  # the 3-star has 4 labellings
+    e3, _ = O.count_mode(L + 1, s, d, 3, undirected=True, per_edge=True)
+    e4, _ = O.count_mode(L + 1, s, d, 4, undirected=True, per_edge=True)
+    assert (e3[:, path3] == L - 1).all() and (e4[:, star] == math.comb(L - 1, 2)).all()
+    # cycle C_n, n >= 5: 3 paths and 4 four-paths through each vertex; 2 and 3 per edge
+    n = 9
+    s, d = _undirected_arcs([(i, (i + 1) % n) for i in range(n)])
+    x3, _ = O.count_mode(n, s, d, 3, undirected=True)
+    x4, _ = O.count_mode(n, s, d, 4, undirected=True)
+    p4 = int(np.nonzero(x4[0])[0][0])
+    assert (x3[:, path3] == 3).all() and (x4[:, p4] == 4).all() and O.classes_undirected(4)[1][p4] == 12
+    e3, _ = O.count_mode(n, s, d, 3, undirected=True, per_edge=True)
+    e4, _ = O.count_mode(n, s, d, 4, undirected=True, per_edge=True)
+    assert (e3[:, path3] == 2).all() and (e4[:, p4] == 3).all()
+
+
+@pytest.mark.parametrize("undirected", [False, True])
+def test_per_edge_totals_identity(undirected):
+    # every set of class m is credited to each of its e_m edges:
+    # sum over edges of Y_m = e_m * (sum over vertices of X_m) / k
+    n, s, d = synth.chung_lu(300, 3.0, 2.3, 21, reciprocity=0.3)
+    for k in (3, 4):
+        canon = (O.classes_undirected(k) if undirected else O.classes(k))[0]
+        x, fx = O.count_mode(n, s, d, k, undirected=undirected)
+        y, fy = O.count_mode(n, s, d, k, undirected=undirected, per_edge=True)
+        assert fx == fy
+        nedges = []
+        for m in canon:
+            bits = [(int(m) >> (k * (k - 1) - 1 - p)) & 1 for p in range(k * (k - 1))]
+            adj = np.zeros((k, k), int)
+            p = 0
+            for i in range(k):
+                for j in range(k):
+                    if i != j:
+                        adj[i, j] = bits[p]
+                        p += 1
+            nedges.append(int(((adj + adj.T) > 0).sum()) // 2)
+        np.testing.assert_array_equal(y.sum(axis=0).astype(object),
+                                      np.array(nedges, dtype=object) * x.sum(axis=0).astype(object) // k)
+        # undirected rows sum to the same number of connected sets as directed ones
+        xd, _ = O.count(n, s, d, k)
+        np.testing.assert_array_equal(x.sum(axis=1), xd.sum(axis=1))
+
+
+@pytest.mark.parametrize("k,seeds", [(3, 200), (4, 60)])
+def test_undirected_gnp_expectation_eq4(k, seeds):
+    # Eq. 4 with n_max = C(k, 2) on undirected G(100, 0.08)
+    n, p = 100, 0.08
+    E = O.gnp_expected_local(n, p, k, undirected=True)
+    per_seed = []
+    for seed in range(seeds):
+        nn, s, d = synth.gnp_undirected(n, p, 20_000 + seed)
+        out, _ = O.count_mode(nn, s, d, k, undirected=True)
+        per_seed.append(out.astype(np.float64).mean(axis=0))
+    per_seed = np.array(per_seed)
+    mean = per_seed.mean(axis=0)
+    sd = per_seed.std(axis=0, ddof=1)
+    big = E * n * seeds >= 200
+    assert big.sum() >= 2
+    se = sd[big] / math.sqrt(seeds)
+    assert np.all(np.abs(mean[big] - E[big]) <= 5 * se + 1e-12), (mean[big], E[big], se)
+    sets_obs = per_seed[:, ~big].sum(axis=0) * n / k
+    sets_exp = E[~big] * n * seeds / k
+    assert np.all(sets_obs <= sets_exp + 8 * np.sqrt(sets_exp) + 12)
