@@ -7,18 +7,22 @@ A step is one vdmc_count over the whole graph (every root, every BFS
 structure), with the graph already resident in HBM.  Prints ONE JSON line.
 
 value      connected k-sets counted per second (instances/s), device time
-           measured with CUDA events on the launching stream.
+           measured with CUDA events on the launching stream.  config splits
+           the sets into those enumerated one by one and those the
+           root-per-CTA kernel accounts for by signature (vdmc_count_stats).
 e2e        the same metric through the public API with HOST buffers: each
            step builds the graph from pinned host arcs (H2D inside), counts,
            and copies the uint64 counts back to pinned host memory.
-roofline   HBM roofline of the counting kernel: algorithmic bytes
-           (vdmc_work_bytes) / launch time against the measured copy peak.
+roofline   HBM roofline of one count: algorithmic bytes (vdmc_work_model:
+           N(r), N(a) per depth-1 vertex, N(b) per distinct depth-2 vertex,
+           output) / device time against the measured copy peak.
 cpu_baseline  the CPU oracle on a bounded root sample of the same graph.
 
 --impl reference times the CPU oracle alone (the reference arm of this
 benchmark), on the host cores, on a bounded sample of the same workload.
-N > 1 (torchrun): N independent replicas, one per GPU (weak scaling); the
-path needs no collective.
+N > 1 (torchrun): one graph, its roots split into N rank ranges of equal
+estimated work (Lemma 1), one count of its range per GPU and one uint64
+sum-reduce of the per-vertex counts (strong scaling).
 """
 from __future__ import annotations
 
@@ -54,9 +58,10 @@ def parse():
     p.add_argument("--batch-graphs", type=int, default=50_000)
     p.add_argument("--batch-compare", type=int, default=2_000,
                    help="graphs of the batch also counted one launch per graph")
-    p.add_argument("--serve-requests", type=int, default=200)
-    p.add_argument("--serve-n-hi", type=int, default=50_000)
-    p.add_argument("--serve-rate", type=float, default=400.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--no-sub", action="store_true", help="skip the 4M-vertex ER and G(100, 0.08) sub-benchmarks")
+    p.add_argument("--serve-requests", type=int, default=2000, help="requests per offered-load point")
+    p.add_argument("--serve-n-hi", type=int, default=100_000)
+    p.add_argument("--serve-loads", default="0.25,0.5,0.75,0.9", help="offered loads (fractions of capacity)")
     p.add_argument("--no-tuned", action="store_true", help="keep the library's default schedule")
     return p.parse_args()
 
@@ -83,18 +88,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def load_traffic(workload, k):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def load_traffic(k, full_alg_bytes):
+    """DRAM bytes per count, from a committed one-launch ncu record of a smaller
+    graph of the same shape (profiles/traffic_small_case.json), scaled to this
+    workload by its algorithmic bytes; None unless the record was taken on the
+    current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic_small_case.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        e = rec.get("%s/k%d" % (workload, k))
+        e = rec.get("k%d" % k)
         if e and e.get("kernel_hash") == kernel_source_hash():
-            return e.get("dram_bytes_per_launch")
+            ratio = e["dram_bytes_per_count"] / e["algorithmic_bytes"]
+            return int(ratio * full_alg_bytes), {"workload": e["workload"], "ratio_to_algorithmic": ratio,
+                                                 "dram_bytes": e["dram_bytes_per_count"],
+                                                 "algorithmic_bytes": e["algorithmic_bytes"]}
     except Exception:
         pass
-    return None
+    return None, None
 
 
 class Clocks:
@@ -174,101 +185,150 @@ def oracle_sample(n, s, d, k, target_s, threads=None):
                       "subtracted)" % (threads, lo, hi, found, k, el, build_s), "lo": lo, "hi": hi}
 
 
-def bench_batch(args, k):
+def timed_ms(fn, reps=3, stream=None):
+    """Best of `reps` device times (CUDA events on the launching stream) after one untimed call."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def launches_per_count(g, schedule):
+    """Kernels one vdmc_count launches: the warp-per-task kernel, the
+    root-per-CTA kernel, the split-root finish and the un-relabel pass."""
+    info = g.info()
+    n_split = min(schedule["hub_split_roots"], info["num_hub_roots"]) if schedule["hub_split"] > 1 else 0
+    return (1 if info["num_tasks"] > 0 else 0) + (1 if info["num_hub_roots"] > 0 else 0) + \
+        (1 if n_split > 0 else 0) + (1 if info["n"] > 0 else 0)
+
+
+def rates(stats, ms):
+    sec = ms / 1e3
+    return {"instances_enumerated": stats["sets_enumerated"], "instances_by_signature": stats["sets_by_signature"],
+            "enumerated_per_s": stats["sets_enumerated"] / sec,
+            "by_signature_per_s": stats["sets_by_signature"] / sec,
+            "stats": stats}
+
+
+def roofline_of(model, ms, peak, peak_kind, kernel, traffic=None, traffic_src=None):
+    achieved = model["bytes"] / (ms / 1e3) / 1e9
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+         "traffic": traffic, "kernel": kernel, "algorithmic_bytes_per_launch": model["bytes"],
+         "peak_kind": "%s hbm_gbs (copy)" % peak_kind,
+         "per_use_model": {"bytes": model["bytes_per_use"],
+                           "frac": model["bytes_per_use"] / (ms / 1e3) / 1e9 / peak},
+         "model": model}
+    if traffic_src:
+        r["traffic_source"] = traffic_src
+    return r
+
+
+def bench_single(name, k, peak, peak_kind, tuned=True, reps=3):
+    """One named single-graph workload: device time per count, instances/s
+    (enumerated / by signature), algorithmic-byte roofline."""
+    import torch
+    from paper_2201_11655_b300 import autotune, synth, vdmc
+    n, s, d = synth.workload(name)
+    saved = vdmc.get_schedule()
+    sched = autotune.apply_tuned(k, n, len(s)) if tuned else None
+    g = vdmc.graph_create(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    try:
+        out = torch.empty((n, vdmc.num_classes(k)), dtype=torch.uint64, device="cuda")
+        ms = timed_ms(lambda: vdmc.count(g, k, out), reps=reps)
+        torch.cuda.synchronize()
+        if g.device_status() != 0:
+            raise RuntimeError("device status error in %s" % name)
+        total = int(out.view(torch.int64).sum().item())
+        if total % k:
+            raise RuntimeError("sum of per-vertex counts is not a multiple of k")
+        inst = total // k
+        stats = g.count_stats()
+        if stats["sets_enumerated"] + stats["sets_by_signature"] != inst:
+            raise RuntimeError("set counters disagree with the counts")
+        model = g.work_model(k)
+        res = {"workload": name, "k": k, "n": n, "arcs": int(len(s)), "ms_per_count": ms,
+               "instances": inst, "instances_per_s": inst / (ms / 1e3),
+               "schedule": vdmc.get_schedule(), "schedule_source": "tuned" if sched else "default",
+               "roofline": roofline_of(model, ms, peak, peak_kind, "vdmc_count (all kernels of one count)")}
+        res.update(rates(stats, ms))
+        return res
+    finally:
+        g.close()
+        vdmc.set_schedule(**saved)
+
+
+def bench_batch(args, ks=(3, 4)):
     """Batched graphs/s: many small uneven graphs (n log-uniform in [10, 500],
     half G(n,p), half Chung-Lu, p ~ U[0.02, 0.2]) counted in one launch over
     their concatenated CSR, against one vdmc_count launch per graph on a
     subset (same pre-built graphs; builds excluded from both), and against
     vdmc_count_batch (cached plan, CUDA-graph replay) on that subset."""
-    import numpy as np
     import torch
-    from paper_2201_11655_b300 import synth, vdmc
-    C = vdmc.num_classes(k)
+    from paper_2201_11655_b300 import autotune, synth, vdmc
     t0 = time.perf_counter()
     graphs = synth.batch(args.batch_graphs, 4)
     gen_s = time.perf_counter() - t0
-
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b2.record()
+    res = {"workload": "%d graphs, n log-uniform [10,500], G(n,p) / Chung-Lu 2.5, p~U[0.02,0.2]" % len(graphs),
+           "generate_s": gen_s}
+    for k in ks:
+        C = vdmc.num_classes(k)
+        saved = vdmc.get_schedule()
+        tuned = None if args.no_tuned else autotune.apply_tuned(k, sum(g[0] for g in graphs),
+                                                                sum(len(g[1]) for g in graphs))
+        try:
+            t0 = time.perf_counter()
+            U = vdmc.graph_create_batch(graphs)
+            build_s = time.perf_counter() - t0
+            out = torch.empty((U.n, C), dtype=torch.uint64, device="cuda")
+            ms_union = timed_ms(lambda: vdmc.count(U, k, out))
+            inst = int(out.view(torch.int64).sum().item()) // k
+            stats = U.count_stats()
+            U.close()
+            sub = graphs[:args.batch_compare]
+            gs = [vdmc.graph_create(n, s, d) for n, s, d in sub]
+            outs = [torch.empty((g.n, C), dtype=torch.uint64, device="cuda") for g in gs]
+            ms_each = timed_ms(lambda: [vdmc.count(g, k, o) for g, o in zip(gs, outs)], reps=1)
+            ms_plan = timed_ms(lambda: vdmc.count_batch(gs, k, outs=outs))
+            Us = vdmc.graph_create_batch(sub)
+            outs_u = torch.empty((Us.n, C), dtype=torch.uint64, device="cuda")
+            ms_union_sub = timed_ms(lambda: vdmc.count(Us, k, outs_u))
+            # identical results: union rows == per-graph counts
+            vdmc.count(Us, k, outs_u)
+            [vdmc.count(g, k, o) for g, o in zip(gs, outs)]
             torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b2))
-        return best
-
-    from paper_2201_11655_b300 import autotune
-    saved = vdmc.get_schedule()
-    tuned = None if args.no_tuned else autotune.apply_tuned(k, sum(g[0] for g in graphs),
-                                                            sum(len(g[1]) for g in graphs))
-    t0 = time.perf_counter()
-    U = vdmc.graph_create_batch(graphs)
-    build_s = time.perf_counter() - t0
-    out = torch.empty((U.n, C), dtype=torch.uint64, device="cuda")
-    ms_union = timed(lambda: vdmc.count(U, k, out))
-    inst = int(out.view(torch.int64).sum().item()) // k
-    U.close()
-    sub = graphs[:args.batch_compare]
-    gs = [vdmc.graph_create(n, s, d) for n, s, d in sub]
-    outs = [torch.empty((g.n, C), dtype=torch.uint64, device="cuda") for g in gs]
-    ms_each = timed(lambda: [vdmc.count(g, k, o) for g, o in zip(gs, outs)], reps=1)
-    ms_plan = timed(lambda: vdmc.count_batch(gs, k, outs=outs))
-    Us = vdmc.graph_create_batch(sub)
-    outs_u = torch.empty((Us.n, C), dtype=torch.uint64, device="cuda")
-    ms_union_sub = timed(lambda: vdmc.count(Us, k, outs_u))
-    # identical results: union rows == per-graph counts
-    vdmc.count(Us, k, outs_u)
-    [vdmc.count(g, k, o) for g, o in zip(gs, outs)]
-    torch.cuda.synchronize()
-    same = all(torch.equal(outs_u[Us.offsets[i]:Us.offsets[i + 1]].view(torch.int64), outs[i].view(torch.int64))
-               for i in range(len(gs)))
-    Us.close()
-    for g in gs:
-        g.close()
-    vdmc.set_schedule(**saved)
-    return {"workload": "%d graphs, n log-uniform [10,500], G(n,p) / Chung-Lu 2.5, p~U[0.02,0.2]" % len(graphs),
-            "schedule": tuned or saved, "schedule_source": "tuned" if tuned else "default",
-            "k": k, "graphs_per_s": len(graphs) / (ms_union / 1e3), "ms_per_batch": ms_union,
-            "instances_per_s": inst / (ms_union / 1e3), "instances": inst, "union_build_s": build_s,
-            "generate_s": gen_s,
-            "subset": {"graphs": len(sub), "one_launch_per_graph_graphs_per_s": len(sub) / (ms_each / 1e3),
-                       "count_batch_replay_graphs_per_s": len(sub) / (ms_plan / 1e3),
-                       "union_graphs_per_s": len(sub) / (ms_union_sub / 1e3), "identical_results": bool(same)}}
+            same = all(torch.equal(outs_u[Us.offsets[i]:Us.offsets[i + 1]].view(torch.int64),
+                                   outs[i].view(torch.int64)) for i in range(len(gs)))
+            Us.close()
+            for g in gs:
+                g.close()
+            r = {"k": k, "schedule": tuned or saved, "schedule_source": "tuned" if tuned else "default",
+                 "graphs_per_s": len(graphs) / (ms_union / 1e3), "ms_per_batch": ms_union,
+                 "instances_per_s": inst / (ms_union / 1e3), "instances": inst, "union_build_s": build_s,
+                 "subset": {"graphs": len(sub), "one_launch_per_graph_graphs_per_s": len(sub) / (ms_each / 1e3),
+                            "count_batch_replay_graphs_per_s": len(sub) / (ms_plan / 1e3),
+                            "union_graphs_per_s": len(sub) / (ms_union_sub / 1e3),
+                            "identical_results": bool(same)}}
+            r.update(rates(stats, ms_union))
+            res["k%d" % k] = r
+        finally:
+            vdmc.set_schedule(**saved)
+    return res
 
 
 def bench_serve(args):
-    """Served requests: Poisson arrivals of count requests over directed
-    Chung-Lu graphs (n log-uniform in [10^3, 5*10^4] by default -- the full
-    [10^3, 2*10^6] stream is a long run, see --serve-n-hi/--serve-requests --
-    mean out-degree U[4,16], exponent U[2.1,2.8], k in {3,4} 50/50) through
-    the continuous-batching loop; throughput and latency."""
-    import torch
-    from paper_2201_11655_b300 import synth
-    from paper_2201_11655_b300.serve import GpuBackend, Request, Server
-    specs = synth.serve_requests(args.serve_requests, 5, rate_hz=args.serve_rate, n_lo=1000, n_hi=args.serve_n_hi)
-    reqs = []
-    for i, sp in enumerate(specs):
-        n, s, d = synth.chung_lu(sp["n"], sp["mean_out_degree"], sp["exponent"], sp["seed"])
-        reqs.append(Request(rid=i, n=n, src=s, dst=d, k=sp["k"], arrival=sp["t"]))
-    free, total = torch.cuda.mem_get_info()
-    budget = int(free * 0.5)
-    srv = Server(GpuBackend(), memory_budget=budget, max_inflight=6, small_n=20_000, batch_max=64,
-                 batch_wait=0.002)
-    t0 = time.perf_counter()
-    srv.submit_stream(reqs)
-    done = srv.run()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    st = Server.latency_stats(done)
-    return {"requests": len(reqs), "rate_hz": args.serve_rate, "n_range": [1000, args.serve_n_hi],
-            "requests_per_s": len(done) / wall, "wall_s": wall, "latency": st,
-            "errors": sum(1 for r in done if r.error), "memory_budget_bytes": budget,
-            "peak_reserved_bytes": srv.peak_reserved,
-            "batches": len({r.job for r in done}), "max_inflight": srv.max_inflight}
+    """Served requests (see paper_2201_11655_b300.serve.sweep): Poisson
+    arrivals swept over offered load, against one plain launch per request."""
+    from paper_2201_11655_b300 import serve
+    return serve.sweep(num=args.serve_requests, n_hi=args.serve_n_hi, loads=args.serve_loads, seed=5)
 
 
 def run_reference(args):
@@ -306,7 +366,6 @@ def run_reference(args):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_2201_11655_b300 import build, synth, vdmc
@@ -333,15 +392,25 @@ def run_ours(args):
     g = vdmc.graph_create(n, src_dev, dst_dev)
     info = g.info()
     del src_dev, dst_dev
+    sharded = world > 1
+    if sharded:
+        # one graph, its roots split into `world` ranges of equal estimated
+        # work (Lemma 1); one uint64 sum-reduce of the partial counts
+        from paper_2201_11655_b300 import shard
+        bounds = shard.partition(g, k, world)
+        count_fn = lambda: shard.count_sharded(g, k, out, bounds, rank, dist)
+    else:
+        count_fn = lambda: vdmc.count(g, k, out)
     out = torch.empty((n, C), dtype=torch.uint64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (126 MB)
 
     for _ in range(args.warmup):
-        vdmc.count(g, k, out)
+        count_fn()
     torch.cuda.synchronize()
     if g.device_status() != 0:
         raise RuntimeError("device status error after warm-up")
-    total = int(out.view(torch.int64).sum().item())
+    ref = out.view(torch.int64).clone()
+    total = int(ref.sum().item())
     if total % k:
         raise RuntimeError("sum of per-vertex counts is not a multiple of k")
     instances = total // k
@@ -354,22 +423,32 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()  # evict L2 between timed launches
             evs[i][0].record(stream)
-            vdmc.count(g, k, out)
+            count_fn()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
+    # the timed counts are checked too: status word clean, output unchanged
+    if g.device_status() != 0:
+        raise RuntimeError("device status error in the timed region")
+    if not torch.equal(out.view(torch.int64), ref):
+        raise RuntimeError("timed counts differ from the warm-up counts")
+    del ref
+    stats = g.count_stats()
+    if not sharded and stats["sets_enumerated"] + stats["sets_by_signature"] != instances:
+        raise RuntimeError("set counters disagree with the counts")
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * instances / (ms / 1e3)
+    # sharded: every rank counts a share of the one graph's sets
+    value = (instances if sharded else world * instances) / (ms / 1e3)
 
     # e2e through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not sharded:
         src_h = torch.from_numpy(s).pin_memory()
         dst_h = torch.from_numpy(d).pin_memory()
         out_h = torch.empty((n, C), dtype=torch.int64).pin_memory()
@@ -391,14 +470,12 @@ def run_ours(args):
                "path": "vdmc_graph_create(host arcs) + vdmc_count + D2H of counts"}
 
     peak, peak_kind = load_peaks()
-    wbytes = g.work_bytes(k)
-    achieved = wbytes / (ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": load_traffic(args.workload, k),
-                "kernel": "vdmc_count: hub_kernel<%d, %d warps> (root-per-CTA) overlapped with count_kernel<%d> "
-                          "(warp-per-task), timed together; traffic = DRAM bytes of all kernels of one count"
-                          % (k, vdmc.get_schedule()["hub_warps"] or 16, k),
-                "algorithmic_bytes_per_launch": wbytes, "peak_kind": "%s hbm_gbs (copy)" % peak_kind}
+    model = g.work_model(k)
+    traffic, traffic_src = load_traffic(k, model["bytes"])
+    roofline = roofline_of(model, ms, peak, peak_kind,
+                           "vdmc_count: hub_kernel<%d, %d warps> (root-per-CTA) overlapped with count_kernel<%d> "
+                           "(warp-per-task), timed together" % (k, vdmc.get_schedule()["hub_warps"] or 16, k),
+                           traffic, traffic_src)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -409,26 +486,35 @@ def run_ours(args):
         except Exception as ex:  # the oracle is a baseline only
             cpu = {"value": None, "unit": "instances/s", "cores": None, "kind": "oracle", "sample": "failed: %s" % ex}
 
+    launches = launches_per_count(g, vdmc.get_schedule()) * args.steps
     g.close()
-    batch = serve = None
-    if rank == 0 and not args.no_batch:
-        batch = bench_batch(args, k)
-    if rank == 0 and not args.no_serve:
-        serve = bench_serve(args)
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_sub:
+        extra["er4m"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, tuned=not args.no_tuned)
+        extra["gnp100"] = {"k3": bench_single("gnp_n100_p0.08", 3, peak, peak_kind, tuned=False),
+                           "k4": bench_single("gnp_n100_p0.08", 4, peak, peak_kind, tuned=False)}
+    if rank == 0 and world == 1 and not args.no_batch:
+        extra["batch"] = bench_batch(args)
+    if rank == 0 and world == 1 and not args.no_serve:
+        extra["serve"] = bench_serve(args)
     if rank == 0:
-        print(json.dumps({
+        cfg = {"workload": args.workload, "k": k, "n": n, "arcs": m, "edges_u": info["edges_u"],
+               "max_degree": info["max_degree"], "instances_per_step": instances,
+               "l2": "256 MB buffer written between timed launches (L2 flush)",
+               "parallelism": ("root-range shards x%d + uint64 all-reduce" % world) if sharded else "single",
+               "schedule": vdmc.get_schedule()}
+        if not sharded:
+            cfg.update(rates(stats, ms))
+        line = {
             "metric": METRIC % k, "value": value, "unit": "instances/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": args.workload, "k": k, "n": n, "arcs": m, "edges_u": info["edges_u"],
-                       "max_degree": info["max_degree"], "instances_per_step": instances,
-                       "l2": "256 MB buffer written between timed launches (L2 flush)",
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "schedule": vdmc.get_schedule()},
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "step_ms": step_ms, "batch": batch, "serve": serve,
-            "schedule_source": "tuned" if tuned else "default",
-        }), flush=True)
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu, "step_ms": step_ms, "schedule_source": "tuned" if tuned else "default",
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

@@ -108,6 +108,23 @@ typedef struct {
 vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                               int ptrs_on_device, void *stream, vdmc_graph **out);
 
+/* Options of vdmc_graph_create_ex. */
+#define VDMC_GRAPH_UNDIRECTED 1u  /* count the undirected motifs of G_U (arc directions ignored) */
+
+/*
+ * vdmc_graph_create with options.  VDMC_GRAPH_UNDIRECTED: the undirected
+ * variant (the undirected motifs the paper reports beside the directed ones,
+ * Tables 1-2 and Fig. 5): every edge of G_U is taken with arcs both ways, so
+ * each connected k-set is classified by its induced undirected graph; counts
+ * of such a graph have vdmc_num_classes_undirected(k) columns (2 for k = 3,
+ * 6 for k = 4), the connected undirected classes in ascending order of the
+ * minimum index of their symmetric adjacency matrix
+ * (vdmc_undirected_class_masks).  Unknown option bits return
+ * VDMC_ERR_INVALID_ARG.  Otherwise as vdmc_graph_create.
+ */
+vdmc_status vdmc_graph_create_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                 int ptrs_on_device, uint32_t options, void *stream, vdmc_graph **out);
+
 /*
  * Build ONE graph from many independent graphs (a batch; no paper
  * counterpart): the disjoint union of graphs 0..num-1.
@@ -130,7 +147,13 @@ vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const in
 vdmc_status vdmc_graph_create_batch(int32_t num, const int32_t *ns, const int64_t *ms, const int32_t *src,
                                     const int32_t *dst, int ptrs_on_device, void *stream, vdmc_graph **out);
 
-/* Free the graph's device memory (synchronises the device first). */
+/* Free the graph's device memory.  Stream-ordered: the frees are queued
+ * behind the graph's last build or count (on whatever stream it ran), so
+ * the call does not wait for the device or for other graphs' work; the
+ * caller must not use the graph, or read an output of a count still in
+ * flight through it, after this call only via the graph handle (outputs
+ * belong to the caller and stay valid).  A graph that led a
+ * vdmc_count_batch plan synchronises the device instead. */
 vdmc_status vdmc_graph_destroy(vdmc_graph *g);
 
 /* Sizes and drop counters of a built graph (host struct, filled in). */
@@ -149,6 +172,18 @@ vdmc_status vdmc_graph_export_csr(const vdmc_graph *g, int64_t *rowptr, uint32_t
 
 /* Number of output columns for k: 13 for k = 3, 199 for k = 4, -1 otherwise. */
 int vdmc_num_classes(int k);
+
+/* Columns of an undirected graph's counts: 2 for k = 3, 6 for k = 4, -1 otherwise. */
+int vdmc_num_classes_undirected(int k);
+
+/* Minimum (symmetric) motif index of each undirected column, ascending
+ * (uint16[vdmc_num_classes_undirected(k)]).  Host-side table. */
+vdmc_status vdmc_undirected_class_masks(int k, uint16_t *canon_out);
+
+/* Columns of g's counts for k: vdmc_num_classes(k), or
+ * vdmc_num_classes_undirected(k) for a graph built with
+ * VDMC_GRAPH_UNDIRECTED; -1 for a bad k or graph. */
+int vdmc_graph_num_classes(const vdmc_graph *g, int k);
 
 /* Minimum motif index of each output column, ascending (uint16[C_k]).
  * Host-side table; needs no device. */
@@ -184,6 +219,30 @@ vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank
                              uint64_t *out_dev, void *stream);
 
 /*
+ * Per-edge counts (the edge variant of the Discussion: a motif credits the
+ * edges it contains instead of its vertices).  For every edge {u, v} of G_U
+ * and class m: the number of connected k-sets containing u and v whose
+ * induced motif is of class m (the edges of a set are the edges of G_U with
+ * both ends in it).  Rows are the edges {u, v}, u < v in ORIGINAL ids, in
+ * ascending (u, v) order -- the order vdmc_graph_edges lists them;
+ * columns as for vdmc_count on this graph (vdmc_graph_num_classes).
+ *   out_dev  device uint64[edges_u * columns], overwritten.  Caller owns it.
+ * Every root is enumerated set by set with the warp-per-task kernel (the
+ * root-per-CTA kernel has no per-edge form), so this costs the number of
+ * sets, not the neighbourhood volume, on graphs with hubs.  The first call
+ * builds an edge index owned by the graph (about 17 bytes per edge).
+ * Asynchronous; calls on one graph must not overlap (as vdmc_count).
+ */
+vdmc_status vdmc_count_edges(vdmc_graph *g, int k, uint64_t *out_dev, void *stream);
+
+/*
+ * The rows of vdmc_count_edges: edge i is {u[i], v[i]}, u[i] < v[i] original
+ * ids, ascending; flags[i] bit 0 = arc u -> v present, bit 1 = arc v -> u.
+ * Host arrays of edges_u entries; any may be NULL.  Synchronous.
+ */
+vdmc_status vdmc_graph_edges(vdmc_graph *g, int32_t *u, int32_t *v, uint8_t *flags);
+
+/*
  * Count `num` independent graphs, built one by one, in ONE launch (a batch
  * of uneven small graphs; no paper counterpart).  outs[i] is a device
  * uint64[n_i * C_k] for graphs[i], overwritten.  `graphs` and `outs` are
@@ -195,23 +254,27 @@ vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, int32_t rank
  * change of graphs, outs, k or schedule rebuilds the plan.  Plans die with
  * graphs[0]; destroying another member graph makes the plan stale, so build
  * a new list after destroying graphs.  Calls on one plan must not overlap.
+ * Directed graphs only (an undirected member returns VDMC_ERR_INVALID_ARG).
+ * Destroying graphs[0] synchronises the device (its plan may have been
+ * replayed on any stream).
  */
 vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t *const *outs,
                              void *stream);
 
 /*
- * Allocation-free count (no counterpart in the paper; an integration aid).
+ * Allocation-free count (the paper has no counterpart; an integration aid).
  *
  * Some callers cannot allocate device memory at the point where they count:
- * code that runs while a CUDA graph is being captured, real-time or serving
- * loops that reserved a fixed device-memory budget at start-up (and where a
- * cudaMalloc could fail, fragment the pool or stall the device), and hosts
- * whose own allocator owns all device memory.  This entry point calls no
- * cudaMalloc, cudaFree or allocating library routine.  It counts with the
- * warp-per-task kernel of vdmc_count (one task per root, no root-per-CTA
- * kernel) and keeps its scratch -- task list, work-queue cursor, status word,
- * class tables -- in one fixed array of about 4.2 MB that every GPU holds
- * for as long as the library is loaded.
+ * real-time or serving loops that reserved a fixed device-memory budget at
+ * start-up (where a cudaMalloc could fail, fragment the pool or stall the
+ * device while it synchronises), and host applications whose own allocator
+ * owns all device memory, so that a library allocating behind their back
+ * would break their accounting.  This entry point calls no cudaMalloc,
+ * cudaFree or allocating library routine.  It counts with the warp-per-task
+ * kernel of vdmc_count (one task per root, no root-per-CTA kernel) and keeps
+ * its scratch -- task list, work-queue cursor, class tables -- in one fixed
+ * array of about 4.2 MB that every GPU holds for as long as the library is
+ * loaded.
  *
  * Inputs are a degree-ordered CSR in the layout vdmc_graph_export_csr
  * returns, in device memory owned by the caller:
@@ -223,20 +286,23 @@ vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int k, uint64_t
  *   new2old    int32[n]: original id of each rank
  *   k          3 or 4
  *   out_dev    uint64[n * C_k], overwritten, rows by original id
- *   status_dev int32 on the device that receives the kernel's status word
- *              (0 = ok, VDMC_ERR_DEVICE_LIMIT = an index check failed), or
- *              NULL to use a word inside the scratch array
+ *   status_dev int32 on the device, required: receives the kernel's status
+ *              word (0 = ok, VDMC_ERR_DEVICE_LIMIT = an index check failed);
+ *              read it after synchronising `stream`
  *   stream     cudaStream_t
- * n above 2^18, k not in {3, 4}, or a NULL input returns
- * VDMC_ERR_INVALID_ARG before any device work.
+ * n above 2^18, k not in {3, 4}, or a NULL pointer (status_dev included)
+ * returns VDMC_ERR_INVALID_ARG before any device work.
  *
  * The first call on a device sets the scratch up (looks up its device
  * address and copies the class tables into it, synchronously); make that
- * first call before any stream capture.  Every call on a device shares the
- * one scratch array and starts by clearing its cursor and status word; calls
- * whose work overlaps on the GPU (different streams, or concurrent host
- * threads) race on it and must be serialised by the caller.  Asynchronous
- * otherwise.
+ * first call before any stream capture.  That set-up is done once per device
+ * for the life of the process: after cudaDeviceReset (or any other teardown
+ * of the device's primary context) this entry point must not be called again
+ * in the same process.  Every call on a device shares the one scratch array,
+ * which keeps the previous call's contents; each call clears its cursor and
+ * the status word it is given before counting.  Calls whose work overlaps on
+ * the GPU (different streams, or concurrent host threads) race on the array
+ * and must be serialised by the caller.  Asynchronous otherwise.
  */
 vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int64_t *rowptr, const uint32_t *col,
                                    const int64_t *pbeg, const int32_t *new2old, int k, uint64_t *out_dev,
@@ -247,17 +313,61 @@ vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int64_t *rowptr
 vdmc_status vdmc_get_device_status(vdmc_graph *g);
 
 /*
- * Measurement hook: the algorithmic byte count of one vdmc_count(g, k) under
- * the current schedule: 4 bytes per adjacency entry the method must read at
- * least once per use -- N(r) for every root, N(a) for every depth-1 vertex
- * of every root and, for k = 4, N(b) for every depth-2 vertex (the
- * root-per-CTA kernel reads the same rows: N(r), N(x) for x in N+(r), N(b)
- * for the Q-neighbours b of each x) -- plus the 8 * n * C_k bytes of the
- * output and 4 * n bytes of the id map.  The cost model of the section on
- * efficacy on simulated graphs: work proportional to the neighbourhoods
- * visited.  Synchronous; runs on the legacy default stream.
+ * Measurement hook: the algorithmic byte model of one vdmc_count(g, k) (the
+ * cost model of the section on efficacy on simulated graphs: work
+ * proportional to the neighbourhoods visited).  Per root r with
+ * P = N+(r), the adjacency rows the method must stream, 4 bytes per entry:
+ * N(r), N(a) for every a in P and, for k = 4, N(b) for every DISTINCT
+ * depth-2 vertex b (rank > r, not adjacent to r, adjacent to some a in P);
+ * plus the 8 * n * C_k bytes of the output and 4 * n bytes of the id map.
+ * `bytes_per_use` counts N(b) once per (a, b) adjacency instead (what an
+ * enumeration without reuse of N(b) streams).  Synchronous; runs on the
+ * legacy default stream.
  */
+typedef struct {
+    uint64_t bytes;                   /* the model above (roofline numerator) */
+    uint64_t bytes_per_use;           /* N(b) counted once per (a, b) */
+    uint64_t entries_root;            /* sum over roots of |N(r)| */
+    uint64_t entries_depth1;          /* sum over roots of sum_{a in P} |N(a)| */
+    uint64_t entries_depth2;          /* k = 4: sum over roots of sum over distinct b of |N(b)| */
+    uint64_t entries_depth2_per_use;  /* k = 4: the same per (a, b) adjacency */
+    uint64_t output_bytes;            /* 8 n C_k + 4 n */
+} vdmc_work_model_t;
+
+vdmc_status vdmc_work_model(const vdmc_graph *g, int k, vdmc_work_model_t *model);
+
+/* vdmc_work_model(g, k).bytes */
 vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes);
+
+/*
+ * Counters of the last count on g (vdmc_count / vdmc_count_roots; read after
+ * synchronising its stream).  Every connected k-set is found either one by
+ * one (the paper's enumeration, and the rare exceptions the root-per-CTA
+ * kernel enumerates) or, for sets rooted at the root-per-CTA kernel's roots,
+ * in bulk through a signature formula; the two are reported apart.
+ * Synchronous.
+ */
+typedef struct {
+    uint64_t sets_plain;           /* sets the warp-per-task kernel enumerated */
+    uint64_t sets_hub;             /* sets rooted at roots of the root-per-CTA kernel */
+    uint64_t sets_hub_enumerated;  /* of those, sets visited one at a time */
+    uint64_t sets_by_signature;    /* sets_hub - sets_hub_enumerated */
+    uint64_t sets_enumerated;      /* sets_plain + sets_hub_enumerated */
+} vdmc_count_stats_t;
+
+vdmc_status vdmc_count_stats(const vdmc_graph *g, vdmc_count_stats_t *stats);
+
+/*
+ * Estimated work of every root (the unit of the root-chunk distribution of
+ * the Discussion: contiguous rank ranges of roots go to different devices,
+ * and by Lemma 1 the ranges' counts sum to the full count).  cost_dev is a
+ * device uint64[n] indexed by RANK: the adjacency entries the root's count
+ * streams (N(r), N(a) for a in N+(r), and for k = 4 N(b) per (a, b) with b at
+ * depth 2), plus C(L, k-1) for roots the warp-per-task kernel enumerates
+ * under the current schedule.  An estimate for balancing, not a count.
+ * Asynchronous on `stream`.
+ */
+vdmc_status vdmc_root_costs(const vdmc_graph *g, int k, uint64_t *cost_dev, void *stream);
 
 /* Global launch schedule (the autotuner's knobs).  Affects later calls. */
 vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s);

@@ -114,32 +114,39 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
 };
 
-void free_union(vdmc_graph *U) {
-    cudaFree(U->rowptr);
-    cudaFree(U->col);
-    cudaFree(U->pbeg);
-    cudaFree(U->new2old);
-    cudaFree(U->old2new);
-    cudaFree(U->tasks);
-    cudaFree(U->qhead);
-    cudaFree(U->status);
-    cudaFree(U->racc);
-    cudaFree(U->d3acc);
-    vdmc_hub_free(U);
+// the plan's union graph; called with the device idle (plan_free)
+void free_union(vdmc_graph *U, cudaStream_t fs) {
+    vdmc_free(U->rowptr, fs);
+    vdmc_free(U->col, fs);
+    vdmc_free(U->pbeg, fs);
+    vdmc_free(U->new2old, fs);
+    vdmc_free(U->old2new, fs);
+    vdmc_free(U->tasks, fs);
+    vdmc_free(U->qhead, fs);
+    vdmc_free(U->status, fs);
+    vdmc_free(U->racc, fs);
+    vdmc_free(U->d3acc, fs);
+    vdmc_free(U->stats, fs);
+    vdmc_hub_free(U, fs);
     if (U->side) cudaStreamDestroy(U->side);
     if (U->ev_fork) cudaEventDestroy(U->ev_fork);
     if (U->ev_join) cudaEventDestroy(U->ev_join);
+    if (U->ev_done) cudaEventDestroy(U->ev_done);
 }
 
+// A plan may have been replayed on any stream, so it is released with the
+// device idle (this is the one release path that synchronises the device).
 void plan_free(Plan *p) {
     if (!p) return;
+    cudaDeviceSynchronize();
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->cap) cudaStreamDestroy(p->cap);
-    free_union(&p->U);
-    cudaFree(p->uout);
-    cudaFree(p->roff_d);
-    cudaFree(p->outs_d);
+    vdmc_free(p->uout, 0);
+    vdmc_free(p->roff_d, 0);
+    vdmc_free(p->outs_d, 0);
+    free_union(&p->U, 0);
+    cudaDeviceSynchronize();
     delete p;
 }
 
@@ -172,26 +179,30 @@ vdmc_status build_plan(vdmc_graph *const *gs, int num, int k, uint64_t *const *o
     U.info.n = (int32_t)N;
     U.serial = vdmc_next_serial();
     VDMC_CUDA_TRY(cudaGetDevice(&U.device));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.rowptr, sizeof(int64_t) * (size_t)(N + 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.col, sizeof(uint32_t) * (size_t)std::max<int64_t>(1, NNZ)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.pbeg, sizeof(int64_t) * (size_t)std::max<int64_t>(1, N)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.new2old, sizeof(int32_t) * (size_t)std::max<int64_t>(1, N)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.qhead, sizeof(unsigned long long)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&U.status, sizeof(int)));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.rowptr, sizeof(int64_t) * (size_t)(N + 1), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.col, sizeof(uint32_t) * (size_t)NNZ, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.pbeg, sizeof(int64_t) * (size_t)N, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.new2old, sizeof(int32_t) * (size_t)N, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.qhead, sizeof(unsigned long long), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.status, sizeof(int), s));
     VDMC_CUDA_TRY(cudaMemsetAsync(U.status, 0, sizeof(int), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&U.stats, sizeof(unsigned long long) * VDMC_NSTATS, s));
     vdmc_status st = vdmc_graph_init_streams(&U);
     if (st != VDMC_OK) return st;
-    VDMC_CUDA_TRY(cudaMalloc((void **)&p->uout, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, N * C)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&p->roff_d, sizeof(int64_t) * (size_t)(num + 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&p->outs_d, sizeof(uint64_t *) * (size_t)num));
+    VDMC_CUDA_TRY(vdmc_malloc(&p->uout, sizeof(uint64_t) * (size_t)(N * C), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&p->roff_d, sizeof(int64_t) * (size_t)(num + 1), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&p->outs_d, sizeof(uint64_t *) * (size_t)num, s));
     int64_t *eoff_d = nullptr;
     PartDesc *parts_d = nullptr;
-    VDMC_CUDA_TRY(cudaMalloc((void **)&eoff_d, sizeof(int64_t) * (size_t)(num + 1)));
-    cudaError_t e = cudaMalloc((void **)&parts_d, sizeof(PartDesc) * (size_t)num);
-    if (e == cudaSuccess) e = cudaMemcpy(p->roff_d, roff.data(), sizeof(int64_t) * (num + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(eoff_d, eoff.data(), sizeof(int64_t) * (num + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(parts_d, parts.data(), sizeof(PartDesc) * num, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(p->outs_d, outs, sizeof(uint64_t *) * num, cudaMemcpyHostToDevice);
+    VDMC_CUDA_TRY(vdmc_malloc(&eoff_d, sizeof(int64_t) * (size_t)(num + 1), s));
+    cudaError_t e = vdmc_malloc(&parts_d, sizeof(PartDesc) * (size_t)num, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->roff_d, roff.data(), sizeof(int64_t) * (num + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(eoff_d, eoff.data(), sizeof(int64_t) * (num + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(parts_d, parts.data(), sizeof(PartDesc) * num, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->outs_d, outs, sizeof(uint64_t *) * num, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         concat_rows<<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(parts_d, num, p->roff_d, eoff_d, N, NNZ,
                                                                      U.rowptr, U.pbeg, U.new2old);
@@ -199,9 +210,9 @@ vdmc_status build_plan(vdmc_graph *const *gs, int num, int k, uint64_t *const *o
             concat_cols<<<(unsigned)((NNZ + 255) / 256), 256, 0, s>>>(parts_d, num, p->roff_d, eoff_d, NNZ, U.col);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(eoff_d);
-    cudaFree(parts_d);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors copied above die with this call
+    vdmc_free(eoff_d, s);
+    vdmc_free(parts_d, s);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
     return vdmc_build_tasks(&U, p->sch.a_chunk, p->sch.hub_min_l, s);
 }
@@ -226,6 +237,7 @@ vdmc_status vdmc_graph_init_streams(vdmc_graph *g) {
     VDMC_CUDA_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
     VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
     VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    VDMC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
     return VDMC_OK;
 }
 
@@ -239,7 +251,7 @@ extern "C" vdmc_status vdmc_count_batch(vdmc_graph *const *graphs, int num, int 
     if (num < 0 || (num > 0 && (!graphs || !outs)) || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
     if (num == 0) return VDMC_OK;
     for (int i = 0; i < num; i++)
-        if (!graphs[i] || (!outs[i] && graphs[i]->n > 0)) return VDMC_ERR_INVALID_ARG;
+        if (!graphs[i] || (!outs[i] && graphs[i]->n > 0) || graphs[i]->undirected) return VDMC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     vdmc_graph *lead = graphs[0];
     Plan *p = (Plan *)lead->batch_plan;
@@ -304,11 +316,11 @@ extern "C" vdmc_status vdmc_graph_create_batch(int32_t num, const int32_t *ns, c
     int32_t *a = nullptr, *b = nullptr;
     int64_t *voff_d = nullptr, *aoff_d = nullptr;
     int *bad = nullptr;
-    cudaError_t e = cudaMalloc((void **)&a, sizeof(int32_t) * (size_t)std::max<int64_t>(1, M));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b, sizeof(int32_t) * (size_t)std::max<int64_t>(1, M));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&voff_d, sizeof(int64_t) * (size_t)(num + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&aoff_d, sizeof(int64_t) * (size_t)(num + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&bad, sizeof(int));
+    cudaError_t e = vdmc_malloc(&a, sizeof(int32_t) * (size_t)M, s);
+    if (e == cudaSuccess) e = vdmc_malloc(&b, sizeof(int32_t) * (size_t)M, s);
+    if (e == cudaSuccess) e = vdmc_malloc(&voff_d, sizeof(int64_t) * (size_t)(num + 1), s);
+    if (e == cudaSuccess) e = vdmc_malloc(&aoff_d, sizeof(int64_t) * (size_t)(num + 1), s);
+    if (e == cudaSuccess) e = vdmc_malloc(&bad, sizeof(int), s);
     const cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(a, src, sizeof(int32_t) * (size_t)M, kind, s);
     if (e == cudaSuccess && M > 0) e = cudaMemcpyAsync(b, dst, sizeof(int32_t) * (size_t)M, kind, s);
@@ -325,12 +337,12 @@ extern "C" vdmc_status vdmc_graph_create_batch(int32_t num, const int32_t *ns, c
     vdmc_status st = VDMC_OK;
     if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
     else if (hbad) st = VDMC_ERR_OUT_OF_RANGE_VERTEX;
-    else st = vdmc_graph_create_grouped((int32_t)N, M, a, b, 1, stream, out, voff_d, num);
-    cudaFree(a);
-    cudaFree(b);
-    cudaFree(voff_d);
-    cudaFree(aoff_d);
-    cudaFree(bad);
+    else st = vdmc_graph_create_grouped((int32_t)N, M, a, b, 1, stream, out, voff_d, num, 0u);
+    vdmc_free(a, s);
+    vdmc_free(b, s);
+    vdmc_free(voff_d, s);
+    vdmc_free(aoff_d, s);
+    vdmc_free(bad, s);
     if (st == VDMC_OK) {
         (*out)->num_graphs = num;
         (*out)->info.arcs_in = M;

@@ -56,7 +56,20 @@ bool weakly_connected(int k, int idx) {
 struct Table {
     std::vector<uint8_t> lut;
     std::vector<uint16_t> canon;
+    // undirected variant: the classes whose matrices are symmetric (an
+    // orbit of a symmetric matrix holds only symmetric matrices, so its name
+    // is the undirected class name); ucol[c] = undirected column of directed
+    // column c, 255 if c is not symmetric
+    std::vector<uint16_t> ucanon;
+    std::vector<uint8_t> ucol;
 };
+
+bool symmetric(int k, int idx) {
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++)
+            if (entry(k, idx, i, j) != entry(k, idx, j, i)) return false;
+    return true;
+}
 
 Table build(int k) {
     const int nidx = 1 << (k * (k - 1));
@@ -91,6 +104,12 @@ Table build(int k) {
         auto it = std::lower_bound(T.canon.begin(), T.canon.end(), (uint16_t)name[idx]);
         T.lut[idx] = (uint8_t)(it - T.canon.begin());
     }
+    T.ucol.assign(T.canon.size(), 255);
+    for (size_t c = 0; c < T.canon.size(); c++)
+        if (symmetric(k, T.canon[c])) {
+            T.ucol[c] = (uint8_t)T.ucanon.size();
+            T.ucanon.push_back(T.canon[c]);
+        }
     return T;
 }
 
@@ -115,6 +134,26 @@ const uint16_t *vdmc_host_canon(int k, int *num_classes) {
     if (!t) return nullptr;
     if (num_classes) *num_classes = (int)t->canon.size();
     return t->canon.data();
+}
+
+const uint8_t *vdmc_host_ucol(int k, int *num_undirected) {
+    const Table *t = table(k);
+    if (!t) return nullptr;
+    if (num_undirected) *num_undirected = (int)t->ucanon.size();
+    return t->ucol.data();
+}
+
+extern "C" int vdmc_num_classes_undirected(int k) {
+    int nu = -1;
+    if (!vdmc_host_ucol(k, &nu)) return -1;
+    return nu;
+}
+
+extern "C" vdmc_status vdmc_undirected_class_masks(int k, uint16_t *canon_out) {
+    const Table *t = table(k);
+    if (!t || !canon_out) return VDMC_ERR_INVALID_ARG;
+    std::copy(t->ucanon.begin(), t->ucanon.end(), canon_out);
+    return VDMC_OK;
 }
 
 extern "C" int vdmc_num_classes(int k) {

@@ -46,6 +46,7 @@ std::mutex g_sched_mu;
 
 struct DevLut {
     uint8_t *lut[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint8_t *ucol[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 DevLut g_lut[64];  // per device
 std::mutex g_lut_mu;
@@ -71,6 +72,31 @@ cudaError_t vdmc_device_lut(int k, const uint8_t **out) {
         g_lut[dev].lut[k] = p;
     }
     *out = g_lut[dev].lut[k];
+    return cudaSuccess;
+}
+
+// directed column -> undirected column (255: not symmetric), per device
+cudaError_t vdmc_device_ucol(int k, const uint8_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_lut_mu);
+    if (!g_lut[dev].ucol[k]) {
+        int nu = 0;
+        const uint8_t *h = vdmc_host_ucol(k, &nu);
+        const size_t bytes = (size_t)(k == 3 ? 13 : 199);
+        uint8_t *p = nullptr;
+        e = cudaMalloc((void **)&p, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return e;
+        }
+        g_lut[dev].ucol[k] = p;
+    }
+    *out = g_lut[dev].ucol[k];
     return cudaSuccess;
 }
 
@@ -100,18 +126,116 @@ __global__ void task_fill(const int64_t *rowptr, const int64_t *pbeg, const int6
     for (int32_t j = 0; j < t; j++) tasks[o + j] = Task{r, j, t, 0};
 }
 
+// Per-edge mode (the edge variant of the Discussion): each set credits the
+// edges of G_U inside it instead of its vertices.  Edge ids: the entries of
+// the upper rows in rank order (the edge {u, v}, u < v in rank, is entry
+// v of u's upper row, id ebase[u] + its position there); erow maps an id to
+// its output row.  ucol maps a directed class to its undirected column
+// (undirected graphs) or is null.
+struct EdgeDesc {
+    const int64_t *ebase;
+    const int64_t *erow;
+    const uint8_t *ucol;
+    int32_t cout;
+};
+
+// id of the edge {u, v} (rank space); -1 (and the status word) if absent
+__device__ __forceinline__ int64_t edge_id(const Csr &g, const int64_t *ebase, uint32_t u, uint32_t v) {
+    if (u > v) {
+        const uint32_t t = u;
+        u = v;
+        v = t;
+    }
+    if (!in_bounds(g, v < g.n)) return -1;
+    const int64_t lo = __ldg(g.pbeg + u), hi = __ldg(g.rowptr + u + 1);
+    const int64_t p = upper_row(g.col, lo, hi, v - 1);  // first entry with rank >= v
+    if (!in_bounds(g, p < hi && (__ldg(g.col + p) >> 2) == v)) return -1;
+    return __ldg(ebase + u) + (p - lo);
+}
+
+__device__ __forceinline__ void edge_credit(const Csr &g, const EdgeDesc &E, uint64_t *out, int64_t eid,
+                                            uint32_t cls) {
+    if (eid < 0) return;
+    const uint32_t c = E.ucol ? (uint32_t)__ldg(E.ucol + cls) : cls;
+    if (!in_bounds(g, c < (uint32_t)E.cout && eid < g.nnz / 2)) return;
+    const int64_t row = __ldg(E.erow + eid);
+    atomicAdd((unsigned long long *)&out[row * E.cout + c], 1ull);
+}
+
+// credits of one set {r, a, b (, c)} to its edges: r-a always (a at position
+// ia of N+(r)); r-b and r-c when b, c are in N+(r) (positions ib, ic >= 0);
+// the other pairs when their flags say they are adjacent
 template <int K>
-__global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const GraphDesc *__restrict__ multi,
+__device__ __forceinline__ void edge_set(const Csr &g, const EdgeDesc &E, uint64_t *out, uint32_t r, uint32_t a,
+                                         uint32_t b, uint32_t c, int32_t ia, int32_t ib, int32_t ic, uint32_t fab,
+                                         uint32_t fac, uint32_t fbc, uint32_t cls) {
+    const int64_t eb = __ldg(E.ebase + r);
+    edge_credit(g, E, out, eb + ia, cls);
+    if (ib >= 0) edge_credit(g, E, out, eb + ib, cls);
+    if (fab) edge_credit(g, E, out, edge_id(g, E.ebase, a, b), cls);
+    if (K == 4) {
+        if (ic >= 0) edge_credit(g, E, out, eb + ic, cls);
+        if (fac) edge_credit(g, E, out, edge_id(g, E.ebase, a, c), cls);
+        if (fbc) edge_credit(g, E, out, edge_id(g, E.ebase, b, c), cls);
+    }
+}
+
+// Neighbour lists staged per warp in shared memory: N+(r) and the parts of
+// N(a) and N(b) above the root (every adjacency test of a set asks about two
+// members of rank > r), when they fit; otherwise the tests search the CSR
+// rows in global memory.
+constexpr int STAGE_P = 64, STAGE_R = 128;
+constexpr int STAGE_WORDS = STAGE_P + 2 * STAGE_R;  // per warp
+
+struct View {
+    const uint32_t *s;  // staged entries (shared memory), or nullptr
+    int64_t beg, end;   // the row segment in col
+};
+
+// warp-wide: copy col[beg, end) to dst when it fits in cap entries
+__device__ __forceinline__ View stage(const Csr &g, uint32_t *dst, int64_t beg, int64_t end, int cap, int lane) {
+    __syncwarp();
+    if (end - beg > cap) return View{nullptr, beg, end};
+    for (int64_t x = beg + lane; x < end; x += 32) dst[x - beg] = __ldg(g.col + x);
+    __syncwarp();
+    return View{dst, beg, end};
+}
+
+__device__ __forceinline__ uint32_t view_entry(const Csr &g, const View &v, int64_t x) {
+    return v.s ? v.s[x - v.beg] : __ldg(g.col + x);
+}
+
+// flags of neighbour u in the view (0 if absent)
+__device__ __forceinline__ uint32_t view_find(const Csr &g, const View &v, uint32_t u) {
+    if (!v.s) return search_row(g.col, v.beg, v.end, u);
+    int32_t lo = 0, len = (int32_t)(v.end - v.beg);
+    while (len > 0) {
+        const int32_t half = len >> 1;
+        if ((v.s[lo + half] >> 2) < u) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    if (lo < (int32_t)(v.end - v.beg) && (v.s[lo] >> 2) == u) return v.s[lo] & 3u;
+    return 0u;
+}
+
+template <int K, bool EDGE>
+__global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const GraphDesc *__restrict__ multi,
                                                    const Task *__restrict__ tasks, int64_t ntasks,
                                                    unsigned long long *qhead, const uint8_t *__restrict__ lut_g,
-                                                   int32_t rank_lo, int32_t rank_hi, int *status) {
+                                                   int32_t rank_lo, int32_t rank_hi, int *status,
+                                                   unsigned long long *stats, EdgeDesc E) {
     constexpr int C = (K == 3) ? 13 : 199;
     constexpr int NIDX = 1 << (K * (K - 1));
     constexpr int NH = (K == 3) ? 2 : 3;  // histograms per warp: r, a (, b)
     extern __shared__ unsigned long long smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    uint8_t *lut = (uint8_t *)(smem + (size_t)nwarps * NH * C);
+    uint32_t *lists = (uint32_t *)(smem + (size_t)nwarps * NH * C) + (size_t)warp * STAGE_WORDS;
+    uint8_t *lut = (uint8_t *)((uint32_t *)(smem + (size_t)nwarps * NH * C) + (size_t)nwarps * STAGE_WORDS);
     const Hist64 hist_r = hist64(smem + (size_t)warp * NH * C, C);
     const Hist64 hist_a = hist64(smem + (size_t)warp * NH * C + C, C);
     const Hist64 hist_b = hist64(smem + (size_t)warp * NH * C + 2 * C, C);  // K == 4 only
@@ -123,12 +247,21 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
     }
     for (int i = threadIdx.x; i < nwarps * NH * C; i += blockDim.x) smem[i] = 0ull;
     __syncthreads();
+    // sets this lane credited (each set is credited by exactly one lane);
+    // summed into stats[0] when the warp runs out of tasks
+    unsigned long long nsets = 0ull;
 
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(qhead, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= (unsigned long long)ntasks) break;
+        if (t >= (unsigned long long)ntasks) {
+            if (stats) {
+                for (int o = 16; o > 0; o >>= 1) nsets += __shfl_xor_sync(0xffffffffu, nsets, o);
+                if (lane == 0 && nsets) atomicAdd(stats, nsets);
+            }
+            break;
+        }
         const Task task = tasks[t];
         const GraphDesc G = multi ? multi[task.g] : single;
         const int32_t r = task.r;
@@ -139,134 +272,150 @@ __global__ void __launch_bounds__(256) count_kernel(GraphDesc single, const Grap
         const int64_t pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
         if (!in_bounds(g, pb >= 0 && pb <= pe && pe <= G.nnz)) continue;
         const int32_t L = (int32_t)(pe - pb);
+        const View VP = stage(g, lists, pb, pe, STAGE_P, lane);  // N+(r)
+        // one set: credit its members (r, a, b through the warp's histograms,
+        // the innermost member directly) or, per edge, its edges
+        auto set3 = [&](uint32_t a, uint32_t b, int32_t ia, int32_t ib, uint32_t fab, uint32_t cls) {
+            if constexpr (EDGE) {
+                edge_set<3>(g, E, out, (uint32_t)r, a, b, 0u, ia, ib, -1, fab, 0u, 0u, cls);
+            } else {
+                hinc(hist_r, cls);
+                hinc(hist_a, cls);
+                credit(g, out, G.new2old, b, C, cls);
+            }
+            nsets++;
+        };
+        auto set4 = [&](uint32_t a, uint32_t b, uint32_t c, int32_t ia, int32_t ib, int32_t ic, uint32_t fab,
+                        uint32_t fac, uint32_t fbc, uint32_t cls) {
+            if constexpr (EDGE) {
+                edge_set<4>(g, E, out, (uint32_t)r, a, b, c, ia, ib, ic, fab, fac, fbc, cls);
+            } else {
+                hinc(hist_r, cls);
+                hinc(hist_a, cls);
+                hinc(hist_b, cls);
+                credit(g, out, G.new2old, c, C, cls);
+            }
+            nsets++;
+        };
 
         for (int32_t ia = task.j; ia < L; ia += task.stride) {
-            const uint32_t ea = __ldg(g.col + pb + ia);
+            const uint32_t ea = view_entry(g, VP, pb + ia);
             const uint32_t a = ea >> 2, fra = ea & 3u;
             if (!in_bounds(g, a < G.n)) break;
             const int64_t a_beg = __ldg(g.rowptr + a), a_end = __ldg(g.rowptr + a + 1);
             if (!in_bounds(g, a_beg >= 0 && a_beg <= a_end && a_end <= G.nnz)) break;
             const int64_t a_up = upper_row(g.col, a_beg, a_end, (uint32_t)r);  // N(a) with rank > r
+            const View VA = stage(g, lists + STAGE_P, a_up, a_end, STAGE_R, lane);
             if (K == 3) {
                 // star: b in P after a
                 for (int32_t ib = ia + 1 + lane; ib < L; ib += 32) {
-                    const uint32_t eb = __ldg(g.col + pb + ib);
+                    const uint32_t eb = view_entry(g, VP, pb + ib);
                     const uint32_t b = eb >> 2, frb = eb & 3u;
-                    const uint32_t cls = lut[mask3(fra, frb, pair_flags(g, a, b))];
+                    const uint32_t fab = view_find(g, VA, b);
+                    const uint32_t cls = lut[mask3(fra, frb, fab)];
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                    hinc(hist_r, cls);
-                    hinc(hist_a, cls);
-                    credit(g, out, G.new2old, b, C, cls);
+                    set3(a, b, ia, ib, fab, cls);
                 }
                 // path: b in N(a) \ N(r), b > r
                 for (int64_t x = a_up + lane; x < a_end; x += 32) {
-                    const uint32_t eb = __ldg(g.col + x);
+                    const uint32_t eb = view_entry(g, VA, x);
                     const uint32_t b = eb >> 2;
-                    if (search_row(g.col, pb, pe, b)) continue;
+                    if (view_find(g, VP, b)) continue;
                     const uint32_t cls = lut[mask3(fra, 0u, eb & 3u)];
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                    hinc(hist_r, cls);
-                    hinc(hist_a, cls);
-                    credit(g, out, G.new2old, b, C, cls);
+                    set3(a, b, ia, -1, eb & 3u, cls);
                 }
             } else {
                 // (A1) b in P after a
                 for (int32_t ib = ia + 1; ib < L; ib++) {
-                    const uint32_t eb = __ldg(g.col + pb + ib);
+                    const uint32_t eb = view_entry(g, VP, pb + ib);
                     const uint32_t b = eb >> 2, frb = eb & 3u;
                     if (!in_bounds(g, b < G.n)) break;
-                    const uint32_t fab = pair_flags(g, a, b);
+                    const uint32_t fab = view_find(g, VA, b);
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
                     if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
+                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
+                    const View VB = stage(g, lists + STAGE_P + STAGE_R, b_up, b_end, STAGE_R, lane);
                     // (1,1,1): c in P after b
                     for (int32_t ic = ib + 1 + lane; ic < L; ic += 32) {
-                        const uint32_t ec = __ldg(g.col + pb + ic);
+                        const uint32_t ec = view_entry(g, VP, pb + ic);
                         const uint32_t c = ec >> 2, frc = ec & 3u;
-                        const uint32_t cls = lut[mask4(fra, frb, frc, fab, pair_flags(g, a, c), pair_flags(g, b, c))];
+                        const uint32_t fac = view_find(g, VA, c), fbc = view_find(g, VB, c);
+                        const uint32_t cls = lut[mask4(fra, frb, frc, fab, fac, fbc)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        hinc(hist_r, cls);
-                        hinc(hist_a, cls);
-                        hinc(hist_b, cls);
-                        credit(g, out, G.new2old, c, C, cls);
+                        set4(a, b, c, ia, ib, ic, fab, fac, fbc, cls);
                     }
                     // (1,1,2) with c in N(a) \ N(r), c > r
                     for (int64_t x = a_up + lane; x < a_end; x += 32) {
-                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t ec = view_entry(g, VA, x);
                         const uint32_t c = ec >> 2;
-                        if (search_row(g.col, pb, pe, c)) continue;
-                        const uint32_t cls = lut[mask4(fra, frb, 0u, fab, ec & 3u, pair_flags(g, b, c))];
+                        if (view_find(g, VP, c)) continue;
+                        const uint32_t fbc = view_find(g, VB, c);
+                        const uint32_t cls = lut[mask4(fra, frb, 0u, fab, ec & 3u, fbc)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        hinc(hist_r, cls);
-                        hinc(hist_a, cls);
-                        hinc(hist_b, cls);
-                        credit(g, out, G.new2old, c, C, cls);
+                        set4(a, b, c, ia, ib, -1, fab, ec & 3u, fbc, cls);
                     }
                     // (1,1,2) with c in N(b) \ N(a) \ N(r), c > r
-                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
                     for (int64_t x = b_up + lane; x < b_end; x += 32) {
-                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t ec = view_entry(g, VB, x);
                         const uint32_t c = ec >> 2;
-                        if (search_row(g.col, pb, pe, c)) continue;
-                        if (pair_flags(g, a, c)) continue;
+                        if (view_find(g, VP, c)) continue;
+                        if (view_find(g, VA, c)) continue;
                         const uint32_t cls = lut[mask4(fra, frb, 0u, fab, 0u, ec & 3u)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        hinc(hist_r, cls);
-                        hinc(hist_a, cls);
-                        hinc(hist_b, cls);
-                        credit(g, out, G.new2old, c, C, cls);
+                        set4(a, b, c, ia, ib, -1, fab, 0u, ec & 3u, cls);
                     }
-                    flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
+                    if (!EDGE) flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
                 }
                 // (A2) b in N(a) \ N(r), b > r
                 for (int64_t xb = a_up; xb < a_end; xb++) {
-                    const uint32_t eb = __ldg(g.col + xb);
+                    const uint32_t eb = view_entry(g, VA, xb);
                     const uint32_t b = eb >> 2, fab = eb & 3u;
                     if (!in_bounds(g, b < G.n)) break;
-                    if (search_row(g.col, pb, pe, b)) continue;  // warp-uniform
+                    if (view_find(g, VP, b)) continue;  // warp-uniform
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
                     if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
+                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
+                    const View VB = stage(g, lists + STAGE_P + STAGE_R, b_up, b_end, STAGE_R, lane);
                     // (1,2,2): c in N(a) after b, c not in N(r)
                     for (int64_t x = xb + 1 + lane; x < a_end; x += 32) {
-                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t ec = view_entry(g, VA, x);
                         const uint32_t c = ec >> 2;
-                        if (search_row(g.col, pb, pe, c)) continue;
-                        const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, ec & 3u, pair_flags(g, b, c))];
+                        if (view_find(g, VP, c)) continue;
+                        const uint32_t fbc = view_find(g, VB, c);
+                        const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, ec & 3u, fbc)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        hinc(hist_r, cls);
-                        hinc(hist_a, cls);
-                        hinc(hist_b, cls);
-                        credit(g, out, G.new2old, c, C, cls);
+                        set4(a, b, c, ia, -1, -1, fab, ec & 3u, fbc, cls);
                     }
                     // (1,2,3): c in N(b), c > r, not in N(r), not adjacent to a
-                    const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
                     for (int64_t x = b_up + lane; x < b_end; x += 32) {
-                        const uint32_t ec = __ldg(g.col + x);
+                        const uint32_t ec = view_entry(g, VB, x);
                         const uint32_t c = ec >> 2;
-                        if (search_row(g.col, pb, pe, c)) continue;
-                        if (pair_flags(g, a, c)) continue;
+                        if (view_find(g, VP, c)) continue;
+                        if (view_find(g, VA, c)) continue;
                         const uint32_t cls = lut[mask4(fra, 0u, 0u, fab, 0u, ec & 3u)];
                         if (!in_bounds(g, cls < (uint32_t)C)) continue;
-                        hinc(hist_r, cls);
-                        hinc(hist_a, cls);
-                        hinc(hist_b, cls);
-                        credit(g, out, G.new2old, c, C, cls);
+                        set4(a, b, c, ia, -1, -1, fab, 0u, ec & 3u, cls);
                     }
-                    flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
+                    if (!EDGE) flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
                 }
             }
-            flush_hist(g, hist_a, C, out, row_of(G.new2old, a), lane);
+            if (!EDGE) flush_hist(g, hist_a, C, out, row_of(G.new2old, a), lane);
         }
-        flush_hist(g, hist_r, C, out, row_of(G.new2old, r), lane);
+        if (!EDGE) flush_hist(g, hist_r, C, out, row_of(G.new2old, r), lane);
     }
 }
 
-// out[new2old[r]] = acc[r] (+ the depth-3 credits d3[r], k = 4), one warp
-// per row (coalesced row copies).  Column d of d3 holds the sets r' - x - b - c
-// credited to c whose class is the d-th smallest of the depth-3 path classes
-// (d3_column); unused columns stay zero.
-__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ d3,
+// out[new2old[r]] = acc[r] (+ the depth-3 credits of r, k = 4), one warp
+// per row (coalesced row copies).  The depth-3 credits are n * VDMC_D3_COLS
+// counters as 32-bit low words d3 followed by as many high words; column d
+// holds the sets r' - x - b - c credited to c whose class is the d-th
+// smallest of the depth-3 path classes (d3_column); unused columns stay zero.
+// With ucol (undirected graphs) directed column c is written to output
+// column ucol[c] of Cout, and skipped when it has none (255).
+__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint32_t *__restrict__ d3,
                                const uint8_t *__restrict__ lut, const int32_t *__restrict__ new2old, int32_t n,
-                               int C, uint64_t *__restrict__ out) {
+                               int C, const uint8_t *__restrict__ ucol, int Cout, uint64_t *__restrict__ out) {
     __shared__ int d3cls[VDMC_D3_COLS];
     if (threadIdx.x < VDMC_D3_COLS) d3cls[threadIdx.x] = -1;
     __syncthreads();
@@ -284,61 +433,117 @@ __global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t 
     for (int c = lane; c < C; c += 32) {
         uint64_t v = acc[r * C + c];
         if (d3) {
+            const uint32_t *d3hi = d3 + (int64_t)n * VDMC_D3_COLS;
             for (int j = 0; j < VDMC_D3_COLS; j++)
-                if (d3cls[j] == c) v += d3[r * VDMC_D3_COLS + j];
+                if (d3cls[j] == c)
+                    v += ((uint64_t)__ldg(d3hi + r * VDMC_D3_COLS + j) << 32) | __ldg(d3 + r * VDMC_D3_COLS + j);
         }
-        out[(int64_t)o * C + c] = v;
+        const int oc = ucol ? (int)__ldg(ucol + c) : c;
+        if (oc < Cout) out[(int64_t)o * Cout + oc] = v;
     }
 }
 
-// Algorithmic bytes of one count: the adjacency rows each method must read
-// at least once per use, 4 bytes per entry.
-//  - roots of the warp-per-task kernel (plain enumeration): N(r), N(a) for
-//    every depth-1 vertex a and, for k = 4, N(b) for every depth-2 vertex b;
-//  - roots of the root-per-CTA kernel (L >= hub_min_l): N(r), N(x) for every
-//    x in N+(r) and, for k = 4, N(b) for every Q-neighbour b of each such x
-//    (counted once per adjacency x-b).
-__global__ void work_bytes_kernel(Csr g, int32_t n, int k, int32_t hub_min_l, unsigned long long *total) {
+// Algorithmic bytes of one count (the cost model of the section on efficacy
+// on simulated graphs: work proportional to the neighbourhoods visited).
+// Per root r with P = N+(r): the adjacency rows the method must stream,
+// 4 bytes per entry -- N(r), N(a) for every a in P and, for k = 4, N(b) for
+// every distinct depth-2 vertex b (rank > r, not adjacent to r, adjacent to
+// some a in P).  One CTA per root; the depth-2 vertices already seen for this
+// root are a bitmap over ranks (shared memory when it fits, else a slice of
+// `gbits` per CTA), cleared again before the next root.  Also counts N(b) once
+// per (a, b) adjacency, the volume an enumeration without reuse streams.
+// tot: [0] entries of N(r), [1] of N(a), [2] of N(b) per distinct b, [3] of
+// N(b) per (a, b).
+__global__ void __launch_bounds__(256) work_model_kernel(Csr g, int32_t n, int k, uint32_t *gbits, int32_t words,
+                                                         int in_smem, unsigned long long *tot) {
+    extern __shared__ uint32_t sbits[];
+    uint32_t *bits = in_smem ? sbits : gbits + (size_t)blockIdx.x * (size_t)words;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = 8;
+    for (int i = tid; i < words; i += 256) bits[i] = 0u;
+    __syncthreads();
+    unsigned long long cr = 0, ca = 0, cbd = 0, cbu = 0;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t rb = __ldg(g.rowptr + r), pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
+        if (tid == 0) cr += (unsigned long long)(pe - rb);
+        if (pe == pb) continue;
+        for (int64_t x = pb + tid; x < pe; x += 256) {
+            const uint32_t a = __ldg(g.col + x) >> 2;
+            ca += (unsigned long long)(__ldg(g.rowptr + a + 1) - __ldg(g.rowptr + a));
+        }
+        if (k != 4) continue;
+        for (int pass = 0; pass < 2; pass++) {  // 0: mark and count, 1: clear
+            for (int64_t x = pb + warp; x < pe; x += NW) {
+                const uint32_t a = __ldg(g.col + x) >> 2;
+                const int64_t ab = __ldg(g.rowptr + a), ae = __ldg(g.rowptr + a + 1);
+                for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r) + lane; y < ae; y += 32) {
+                    const uint32_t b = __ldg(g.col + y) >> 2;
+                    if (search_row(g.col, pb, pe, b)) continue;  // b in P: depth 1
+                    if (pass == 1) {
+                        bits[b >> 5] = 0u;
+                        continue;
+                    }
+                    const unsigned long long db = (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
+                    cbu += db;
+                    const uint32_t m = 1u << (b & 31u);
+                    if (!(atomicOr(bits + (b >> 5), m) & m)) cbd += db;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    unsigned long long v[4] = {cr, ca, cbd, cbu};
+    for (int i = 0; i < 4; i++) {
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+        if (lane == 0 && v[i]) atomicAdd(tot + i, v[i]);
+    }
+}
+
+// Estimated work of each root, for splitting the roots into ranges of
+// equal work (the root-chunk distribution of the Discussion): the adjacency
+// entries its count streams -- N(r), N(a) for a in P and, for k = 4, N(b) for
+// every (a, b) with b a depth-2 vertex -- plus, for a root of the
+// warp-per-task kernel (L < hub_min_l, or hub_min_l = 0), the C(L, k-1)
+// star-shaped sets it enumerates one by one.  One warp per root.
+__global__ void root_cost_kernel(Csr g, int32_t n, int k, int32_t hub_min_l, unsigned long long *cost) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long acc = 0;
     for (int64_t r = wid; r < n; r += nw) {
         const int64_t rb = __ldg(g.rowptr + r), pb = __ldg(g.pbeg + r), pe = __ldg(g.rowptr + r + 1);
-        const bool hub = hub_min_l > 0 && pe - pb >= hub_min_l;
-        if (lane == 0) acc += (unsigned long long)(pe - rb);
+        unsigned long long acc = 0;
         for (int64_t x = pb + lane; x < pe; x += 32) {
             const uint32_t a = __ldg(g.col + x) >> 2;
             const int64_t ab = __ldg(g.rowptr + a), ae = __ldg(g.rowptr + a + 1);
             acc += (unsigned long long)(ae - ab);
-            if (k == 4) {
+            if (k == 4)
                 for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r); y < ae; y++) {
                     const uint32_t b = __ldg(g.col + y) >> 2;
-                    if (search_row(g.col, pb, pe, b)) continue;
-                    acc += (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
+                    if (!search_row(g.col, pb, pe, b))
+                        acc += (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
                 }
-            } else if (hub) {
-                // k = 3 signature counting reads N(b) of each Q-neighbour once
-                for (int64_t y = upper_row(g.col, ab, ae, (uint32_t)r); y < ae; y++) {
-                    const uint32_t b = __ldg(g.col + y) >> 2;
-                    if (search_row(g.col, pb, pe, b)) continue;
-                    acc += (unsigned long long)(__ldg(g.rowptr + b + 1) - __ldg(g.rowptr + b));
-                }
-            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const unsigned long long L = (unsigned long long)(pe - pb);
+            const bool plain = hub_min_l == 0 || (int64_t)L < hub_min_l;
+            unsigned long long sets = 0;
+            if (plain && L >= (unsigned long long)(k - 1))
+                sets = k == 3 ? L * (L - 1) / 2 : L * (L - 1) / 2 * (L - 2) / 3;
+            cost[r] = acc + (unsigned long long)(pe - rb) + sets;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0 && acc) atomicAdd(total, acc * 4ull);
 }
 
 size_t smem_bytes(int k, int warps) {
     int C = k == 3 ? 13 : 199, NH = k == 3 ? 2 : 3;
-    return (size_t)warps * NH * C * sizeof(unsigned long long) + ((size_t)1 << (k * (k - 1)));
+    return (size_t)warps * NH * C * sizeof(unsigned long long) + (size_t)warps * STAGE_WORDS * sizeof(uint32_t) +
+           ((size_t)1 << (k * (k - 1)));
 }
 
 vdmc_status launch_count(int k, const GraphDesc &single, const GraphDesc *multi, const Task *tasks,
                          int64_t ntasks, unsigned long long *qhead, int32_t lo, int32_t hi, int *status,
-                         cudaStream_t s) {
+                         unsigned long long *stats, cudaStream_t s, bool edge = false, EdgeDesc E = EdgeDesc{}) {
     const uint8_t *lut = nullptr;
     VDMC_CUDA_TRY(device_lut(k, &lut));
     vdmc_schedule_t sch;
@@ -349,7 +554,8 @@ vdmc_status launch_count(int k, const GraphDesc &single, const GraphDesc *multi,
     int dev = 0, sms = 0;
     VDMC_CUDA_TRY(cudaGetDevice(&dev));
     VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    auto kern = (k == 3) ? count_kernel<3> : count_kernel<4>;
+    auto kern = edge ? ((k == 3) ? count_kernel<3, true> : count_kernel<4, true>)
+                     : ((k == 3) ? count_kernel<3, false> : count_kernel<4, false>);
     VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -360,7 +566,8 @@ vdmc_status launch_count(int k, const GraphDesc &single, const GraphDesc *multi,
     if (grid > need) grid = std::max<int64_t>(1, need);
     VDMC_CUDA_TRY(cudaMemsetAsync(qhead, 0, sizeof(unsigned long long), s));
     if (ntasks > 0) {
-        kern<<<(unsigned)grid, threads, smem, s>>>(single, multi, tasks, ntasks, qhead, lut, lo, hi, status);
+        kern<<<(unsigned)grid, threads, smem, s>>>(single, multi, tasks, ntasks, qhead, lut, lo, hi, status, stats,
+                                                   E);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     return VDMC_OK;
@@ -375,7 +582,7 @@ void vdmc_current_schedule(vdmc_schedule_t *s) {
 
 vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, cudaStream_t s) {
     if (a_chunk < 1 || hub_min_l < 0) return VDMC_ERR_INVALID_ARG;
-    cudaFree(g->tasks);
+    vdmc_free(g->tasks, s);  // stream-ordered behind the last count on s
     g->tasks = nullptr;
     g->ntasks = 0;
     const int32_t n = g->n;
@@ -389,7 +596,7 @@ vdmc_status vdmc_build_tasks(vdmc_graph *g, int32_t a_chunk, int32_t hub_min_l, 
     int64_t total = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cnt + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&g->tasks, sizeof(Task) * (size_t)(total ? total : 1));
+    if (e == cudaSuccess) e = vdmc_malloc(&g->tasks, sizeof(Task) * (size_t)total, s);
     if (e == cudaSuccess && n > 0) {
         task_fill<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, cnt, n, a_chunk, hub_min_l, g->tasks);
         e = cudaGetLastError();
@@ -405,6 +612,11 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     if (!g || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
     if (!out && g->n > 0) return VDMC_ERR_INVALID_ARG;
     const int C = k == 3 ? 13 : 199;
+    cudaStreamCaptureStatus cs0 = cudaStreamCaptureStatusNone;
+    VDMC_CUDA_TRY(cudaStreamIsCapturing(s, &cs0));
+    // the previous build or count of this graph (on any stream) comes first:
+    // its buffers may be freed or reused below
+    if (cs0 == cudaStreamCaptureStatusNone) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
     vdmc_schedule_t sch;
     vdmc_current_schedule(&sch);
     if (g->tasks_a_chunk != sch.a_chunk || g->hub_min_l != sch.hub_min_l) {
@@ -414,20 +626,16 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     // Credits accumulate in a rank-space array owned by the graph (no id-map
     // load in front of each atomic); one coalesced pass then writes every row
     // to its original id in `out`.
-    if (!g->racc && g->n > 0) {
-        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-        VDMC_CUDA_TRY(cudaMalloc((void **)&g->racc, sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES));
-    }
+    if (!g->racc && g->n > 0)
+        VDMC_CUDA_TRY(vdmc_malloc(&g->racc, sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES, s));
     uint64_t *acc = g->racc;
     if (g->n > 0) VDMC_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(uint64_t) * (size_t)g->n * C, s));
+    if (g->stats) VDMC_CUDA_TRY(cudaMemsetAsync(g->stats, 0, sizeof(unsigned long long) * VDMC_NSTATS, s));
     // depth-3 credits of the root-per-CTA kernel (k = 4): one column per path
     // class (16 per vertex) instead of 199, so that more reductions stay in L2
     uint64_t *d3 = nullptr;
     if (k == 4 && g->nhubs > 0 && g->n > 0) {
-        if (!g->d3acc) {
-            VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-            VDMC_CUDA_TRY(cudaMalloc((void **)&g->d3acc, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS));
-        }
+        if (!g->d3acc) VDMC_CUDA_TRY(vdmc_malloc(&g->d3acc, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
         d3 = g->d3acc;
         VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
     }
@@ -444,14 +652,80 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
     }
-    vdmc_status st = launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, s);
+    vdmc_status st = launch_count(k, d, nullptr, g->tasks, g->ntasks, g->qhead, lo, hi, g->status, g->stats, s);
     if (g->nhubs > 0) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
     if (st != VDMC_OK) return st;
     if (g->n > 0) {
-        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, d3, lut, g->new2old, g->n, C, out);
+        const uint8_t *ucol = nullptr;
+        if (g->undirected) VDMC_CUDA_TRY(vdmc_device_ucol(k, &ucol));
+        const int Cout = g->undirected ? vdmc_num_classes_undirected(k) : C;
+        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, reinterpret_cast<const uint32_t *>(d3), lut,
+                                                                   g->new2old, g->n, C, ucol, Cout, out);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
+    // the graph's memory is released behind this point (vdmc_graph_destroy);
+    // a captured count (batch plans) is ordered by its replays instead
+    if (cs0 == cudaStreamCaptureStatusNone) VDMC_CUDA_TRY(cudaEventRecord(g->ev_done, s));
     return VDMC_OK;
+}
+
+extern "C" int vdmc_graph_num_classes(const vdmc_graph *g, int k) {
+    if (!g || (k != 3 && k != 4)) return -1;
+    return g->undirected ? vdmc_num_classes_undirected(k) : vdmc_num_classes(k);
+}
+
+// Per-edge counts (edges.cu builds the edge index): the warp-per-task kernel
+// over every root, crediting edges; out has one row per edge of G_U in
+// (min, max) original-id order.
+vdmc_status vdmc_count_edges_internal(vdmc_graph *g, int k, uint64_t *out, cudaStream_t s) {
+    if (!g || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
+    const int64_t ne = g->nnz / 2;
+    if (!out && ne > 0) return VDMC_ERR_INVALID_ARG;
+    VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_done, 0));
+    vdmc_status st = vdmc_edge_index(g, s);
+    if (st != VDMC_OK) return st;
+    vdmc_schedule_t sch;
+    vdmc_current_schedule(&sch);
+    if (!g->etasks || g->etasks_a_chunk != sch.a_chunk) {
+        // every root with a higher-rank neighbour (the root-per-CTA kernel
+        // has no per-edge form)
+        vdmc_free(g->etasks, s);
+        g->etasks = nullptr;
+        g->netasks = 0;
+        const int32_t n = g->n;
+        int64_t *cnt = nullptr;
+        VDMC_CUDA_TRY(vdmc_malloc(&cnt, sizeof(int64_t) * ((size_t)n + 1), s));
+        if (n > 0) task_counts<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, n, sch.a_chunk, 0, cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = vdmc_exclusive_scan_i64(cnt, cnt, n, s);
+        int64_t total = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, cnt + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = vdmc_malloc(&g->etasks, sizeof(Task) * (size_t)total, s);
+        if (e == cudaSuccess && n > 0) {
+            task_fill<<<(n + 255) / 256, 256, 0, s>>>(g->rowptr, g->pbeg, cnt, n, sch.a_chunk, 0, g->etasks);
+            e = cudaGetLastError();
+        }
+        vdmc_free(cnt, s);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
+        g->netasks = total;
+        g->etasks_a_chunk = sch.a_chunk;
+    }
+    const int Cout = g->undirected ? vdmc_num_classes_undirected(k) : (k == 3 ? 13 : 199);
+    const uint8_t *ucol = nullptr;
+    if (g->undirected) VDMC_CUDA_TRY(vdmc_device_ucol(k, &ucol));
+    if (ne > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)ne * Cout, s));
+    if (g->stats) VDMC_CUDA_TRY(cudaMemsetAsync(g->stats, 0, sizeof(unsigned long long) * VDMC_NSTATS, s));
+    GraphDesc d{g->rowptr, g->col, g->pbeg, nullptr, out, g->n, 0, g->nnz};
+    st = launch_count(k, d, nullptr, g->etasks, g->netasks, g->qhead, 0, g->n, g->status, g->stats, s, true,
+                      EdgeDesc{g->ebase, g->erow, ucol, Cout});
+    if (st != VDMC_OK) return st;
+    VDMC_CUDA_TRY(cudaEventRecord(g->ev_done, s));
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_count_edges(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {
+    return vdmc_count_edges_internal(g, k, out_dev, (cudaStream_t)stream);
 }
 
 extern "C" vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream) {
@@ -464,24 +738,75 @@ extern "C" vdmc_status vdmc_count_roots(vdmc_graph *g, int k, int32_t rank_lo, i
     return vdmc_count_internal(g, k, rank_lo, std::min(rank_hi, g->n), out_dev, (cudaStream_t)stream);
 }
 
-extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes) {
-    if (!g || !bytes || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
-    unsigned long long *d = nullptr;
-    VDMC_CUDA_TRY(cudaMalloc((void **)&d, sizeof(unsigned long long)));
-    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess && g->n > 0) {
-        Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
-        vdmc_schedule_t sch;
-        vdmc_current_schedule(&sch);
-        work_bytes_kernel<<<1184, 256>>>(c, g->n, k, sch.hub_min_l, d);
-        e = cudaGetLastError();
-    }
-    unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
-    cudaFree(d);
-    if (e != cudaSuccess) return VDMC_ERR_CUDA;
+extern "C" vdmc_status vdmc_work_model(const vdmc_graph *g, int k, vdmc_work_model_t *m) {
+    if (!g || !m || (k != 3 && k != 4)) return VDMC_ERR_INVALID_ARG;
+    std::memset(m, 0, sizeof *m);
     const int C = k == 3 ? 13 : 199;
-    *bytes = (uint64_t)h + 8ull * (uint64_t)g->n * (uint64_t)C + 4ull * (uint64_t)g->n;
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (g->n > 0) {
+        int dev = 0, sms = 0;
+        VDMC_CUDA_TRY(cudaGetDevice(&dev));
+        VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int32_t words = (int32_t)(((int64_t)g->n + 31) / 32);
+        const bool in_smem = words <= 46000;  // 184 KB of shared memory
+        const int grid = std::max(1, std::min(g->n, sms * (in_smem ? 1 : 2)));
+        unsigned long long *d = nullptr;
+        uint32_t *gbits = nullptr;
+        VDMC_CUDA_TRY(cudaMalloc((void **)&d, sizeof h));
+        cudaError_t e = cudaMemset(d, 0, sizeof h);
+        if (e == cudaSuccess && !in_smem) e = cudaMalloc((void **)&gbits, sizeof(uint32_t) * (size_t)words * grid);
+        const size_t dsm = in_smem ? sizeof(uint32_t) * (size_t)words : 0;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(work_model_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        if (e == cudaSuccess) {
+            Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
+            work_model_kernel<<<grid, 256, dsm>>>(c, g->n, k, gbits, words, in_smem ? 1 : 0, d);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+        cudaFree(d);
+        cudaFree(gbits);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
+    }
+    m->entries_root = h[0];
+    m->entries_depth1 = h[1];
+    m->entries_depth2 = k == 4 ? h[2] : 0;
+    m->entries_depth2_per_use = k == 4 ? h[3] : 0;
+    m->output_bytes = 8ull * (uint64_t)g->n * (uint64_t)C + 4ull * (uint64_t)g->n;
+    m->bytes = 4ull * (m->entries_root + m->entries_depth1 + m->entries_depth2) + m->output_bytes;
+    m->bytes_per_use = 4ull * (m->entries_root + m->entries_depth1 + m->entries_depth2_per_use) + m->output_bytes;
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_work_bytes(const vdmc_graph *g, int k, uint64_t *bytes) {
+    if (!bytes) return VDMC_ERR_INVALID_ARG;
+    vdmc_work_model_t m;
+    const vdmc_status st = vdmc_work_model(g, k, &m);
+    if (st == VDMC_OK) *bytes = m.bytes;
+    return st;
+}
+
+extern "C" vdmc_status vdmc_count_stats(const vdmc_graph *g, vdmc_count_stats_t *out) {
+    if (!g || !out) return VDMC_ERR_INVALID_ARG;
+    unsigned long long h[VDMC_NSTATS] = {0, 0, 0, 0};
+    if (g->stats) VDMC_CUDA_TRY(cudaMemcpy(h, g->stats, sizeof h, cudaMemcpyDeviceToHost));
+    out->sets_plain = h[0];
+    out->sets_hub = h[1];
+    out->sets_hub_enumerated = h[2];
+    out->sets_by_signature = h[1] >= h[2] ? h[1] - h[2] : 0;
+    out->sets_enumerated = h[0] + h[2];
+    return VDMC_OK;
+}
+
+extern "C" vdmc_status vdmc_root_costs(const vdmc_graph *g, int k, uint64_t *cost_dev, void *stream) {
+    if (!g || (k != 3 && k != 4) || (g->n > 0 && !cost_dev)) return VDMC_ERR_INVALID_ARG;
+    if (g->n == 0) return VDMC_OK;
+    vdmc_schedule_t sch;
+    vdmc_current_schedule(&sch);
+    Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
+    const int64_t blocks = std::min<int64_t>(((int64_t)g->n * 32 + 255) / 256, 148 * 16);
+    root_cost_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(c, g->n, k, sch.hub_min_l,
+                                                                         (unsigned long long *)cost_dev);
+    VDMC_CUDA_TRY(cudaGetLastError());
     return VDMC_OK;
 }
 
@@ -504,15 +829,18 @@ extern "C" vdmc_status vdmc_get_schedule(vdmc_schedule_t *s) {
 // ------------------------------------------------- allocation-free variant --
 //
 // vdmc_count_csr_noalloc: the warp-per-task count for callers that must not
-// allocate device memory.  Its scratch (task list, work-queue cursor,
-// status word, class tables) is the file-scope array below, which exists
-// once per device for as long as the library is loaded.
+// allocate device memory (a fixed device-memory budget reserved up front, or
+// a host allocator that owns the device).  Its scratch (task list,
+// work-queue cursor, class tables) is the file-scope array below, which
+// exists once per device for as long as the library is loaded.  Its device
+// address is looked up once per device, with that device current; a reset of
+// the device's primary context is not supported afterwards.
 
 namespace {
 
 constexpr int64_t NOALLOC_MAX_N = int64_t(1) << 18;       // vertices
 constexpr int64_t NOALLOC_MAX_TASKS = NOALLOC_MAX_N;      // one per root with L >= 1 at most
-constexpr size_t NOALLOC_HDR = 256;                        // cursor (8 B) + status (4 B), padded
+constexpr size_t NOALLOC_HDR = 256;                        // cursor (8 B), padded
 constexpr size_t NOALLOC_LUT = 4096 + 64;                  // k = 4 table, then k = 3 table
 constexpr size_t NOALLOC_BYTES = NOALLOC_HDR + NOALLOC_LUT + sizeof(Task) * (size_t)NOALLOC_MAX_TASKS;
 
@@ -576,6 +904,7 @@ extern "C" vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int6
                                               int *status_dev, void *stream) {
     if (k != 3 && k != 4) return VDMC_ERR_INVALID_ARG;
     if (n < 0 || nnz < 0 || n > NOALLOC_MAX_N) return VDMC_ERR_INVALID_ARG;
+    if (!status_dev) return VDMC_ERR_INVALID_ARG;  // a lost status word would hide a failed index check
     if (n > 0 && (!rowptr || !pbeg || !new2old || !out_dev || (nnz > 0 && !col))) return VDMC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
@@ -600,7 +929,7 @@ extern "C" vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int6
     }
     const int C = k == 3 ? 13 : 199;
     unsigned long long *cursor = (unsigned long long *)base;
-    int *status = status_dev ? status_dev : (int *)(base + 8);
+    int *status = status_dev;
     const uint8_t *lut = base + NOALLOC_HDR + (k == 4 ? 0 : 4096);
     Task *tasks = (Task *)(base + NOALLOC_HDR + NOALLOC_LUT);
     if (n == 0) return VDMC_OK;
@@ -613,12 +942,13 @@ extern "C" vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int6
     const size_t smem = smem_bytes(k, warps);
     int sms = 0, per_sm = 0;
     VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    auto kern = (k == 3) ? count_kernel<3> : count_kernel<4>;
+    auto kern = (k == 3) ? count_kernel<3, false> : count_kernel<4, false>;
     VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
     const int64_t grid = (int64_t)sms * std::max(1, per_sm);
     GraphDesc d{rowptr, col, pbeg, new2old, out_dev, n, 0, nnz};
-    kern<<<(unsigned)grid, warps * 32, smem, s>>>(d, nullptr, tasks, NOALLOC_MAX_TASKS, cursor, lut, 0, n, status);
+    kern<<<(unsigned)grid, warps * 32, smem, s>>>(d, nullptr, tasks, NOALLOC_MAX_TASKS, cursor, lut, 0, n, status,
+                                                  nullptr, EdgeDesc{});
     VDMC_CUDA_TRY(cudaGetLastError());
     return VDMC_OK;
 }

@@ -155,14 +155,15 @@ __global__ void oriented_entries(const uint64_t *__restrict__ uedges, int64_t eu
     out[2 * i + 1] = (ry * (uint64_t)n + rx) | (fswap << 62);
 }
 
+// or_flags = 3 for an undirected graph: every edge is taken as arcs both ways
 __global__ void fill_col(const uint64_t *__restrict__ sorted, int64_t nnz, int32_t n, const int64_t *rowptr,
-                         uint32_t *__restrict__ col, int64_t *__restrict__ pbeg) {
+                         uint32_t *__restrict__ col, int64_t *__restrict__ pbeg, uint32_t or_flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nnz) return;
     uint64_t k = sorted[i];
     uint64_t lo = k & LOW_MASK;
     uint32_t row = (uint32_t)(lo / (uint64_t)n), c = (uint32_t)(lo % (uint64_t)n);
-    col[i] = (c << 2) | (uint32_t)(k >> 62);
+    col[i] = (c << 2) | (uint32_t)(k >> 62) | or_flags;
     if (c > row) {
         bool first = (i == rowptr[row]);
         if (!first) {
@@ -205,32 +206,47 @@ struct Tmp {
     }
 };
 
+// Stream-ordered release: the frees are queued on the graph's side stream
+// behind its last build or count step (ev_done), so destroying a graph waits
+// for nothing else on the device.
 void free_graph_buffers(vdmc_graph *g) {
-    cudaFree(g->rowptr);
-    cudaFree(g->col);
-    cudaFree(g->pbeg);
-    cudaFree(g->new2old);
-    cudaFree(g->old2new);
-    cudaFree(g->tasks);
-    cudaFree(g->qhead);
-    cudaFree(g->status);
-    vdmc_hub_free(g);
+    cudaStream_t fs = g->side;
+    if (fs && g->ev_done) cudaStreamWaitEvent(fs, g->ev_done, 0);
+    vdmc_free(g->rowptr, fs);
+    vdmc_free(g->col, fs);
+    vdmc_free(g->pbeg, fs);
+    vdmc_free(g->new2old, fs);
+    vdmc_free(g->old2new, fs);
+    vdmc_free(g->tasks, fs);
+    vdmc_free(g->qhead, fs);
+    vdmc_free(g->status, fs);
+    vdmc_hub_free(g, fs);
     vdmc_batch_plan_free(g);
-    cudaFree(g->racc);
-    cudaFree(g->d3acc);
-    if (g->side) cudaStreamDestroy(g->side);
+    vdmc_free(g->racc, fs);
+    vdmc_free(g->d3acc, fs);
+    vdmc_free(g->stats, fs);
+    vdmc_free(g->ebase, fs);
+    vdmc_free(g->erow, fs);
+    vdmc_free(g->ekeys, fs);
+    vdmc_free(g->eflags, fs);
+    vdmc_free(g->etasks, fs);
+    if (g->side) cudaStreamDestroy(g->side);  // released once its queued frees have run
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->ev_done) cudaEventDestroy(g->ev_done);
 }
 
 vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int on_device,
-                        cudaStream_t s, vdmc_graph *g, const int64_t *goff, int32_t ngroups) {
+                        cudaStream_t s, vdmc_graph *g, const int64_t *goff, int32_t ngroups, uint32_t options) {
     g->n = n;
+    g->undirected = (options & VDMC_GRAPH_UNDIRECTED) ? 1 : 0;
     g->info.n = n;
     g->info.arcs_in = m;
     VDMC_CUDA_TRY(cudaGetDevice(&g->device));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->qhead, sizeof(unsigned long long)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->status, sizeof(int)));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->qhead, sizeof(unsigned long long), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->status, sizeof(int), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->stats, sizeof(unsigned long long) * VDMC_NSTATS, s));
+    VDMC_CUDA_TRY(cudaMemsetAsync(g->stats, 0, sizeof(unsigned long long) * VDMC_NSTATS, s));
     {
         vdmc_status st0 = vdmc_graph_init_streams(g);
         if (st0 != VDMC_OK) return st0;
@@ -305,11 +321,11 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     // 3: degrees and ranks
     const int64_t nnz = 2 * eu;
     g->nnz = nnz;
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->rowptr, sizeof(int64_t) * ((size_t)n + 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->col, sizeof(uint32_t) * (size_t)(nnz ? nnz : 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->pbeg, sizeof(int64_t) * (size_t)(n ? n : 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->new2old, sizeof(int32_t) * (size_t)(n ? n : 1)));
-    VDMC_CUDA_TRY(cudaMalloc((void **)&g->old2new, sizeof(int32_t) * (size_t)(n ? n : 1)));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->rowptr, sizeof(int64_t) * ((size_t)n + 1), s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->col, sizeof(uint32_t) * (size_t)nnz, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->pbeg, sizeof(int64_t) * (size_t)n, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->new2old, sizeof(int32_t) * (size_t)n, s));
+    VDMC_CUDA_TRY(vdmc_malloc(&g->old2new, sizeof(int32_t) * (size_t)n, s));
     int32_t *deg;
     int64_t *deg_rank;
     uint64_t *rk, *rk2, *rsorted;
@@ -359,7 +375,8 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
             VDMC_CUDA_TRY(cudaGetLastError());
         }
         if (nnz > 0) {
-            fill_col<<<blocks_for(nnz, 256), 256, 0, s>>>(csorted, nnz, n, g->rowptr, g->col, g->pbeg);
+            fill_col<<<blocks_for(nnz, 256), 256, 0, s>>>(csorted, nnz, n, g->rowptr, g->col, g->pbeg,
+                                                          g->undirected ? 3u : 0u);
             VDMC_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -377,26 +394,32 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     vdmc_current_schedule(&sch);
     vdmc_status st = vdmc_build_tasks(g, sch.a_chunk, sch.hub_min_l, s);
     if (st != VDMC_OK) return st;
+    VDMC_CUDA_TRY(cudaEventRecord(g->ev_done, s));
     VDMC_CUDA_TRY(cudaStreamSynchronize(s));
     return VDMC_OK;
 }
 
 }  // namespace
 
-vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
-                                      int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
-                                      int32_t ngroups);
-
 extern "C" vdmc_status vdmc_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                          int ptrs_on_device, void *stream, vdmc_graph **out) {
-    return vdmc_graph_create_grouped(n, m, src, dst, ptrs_on_device, stream, out, nullptr, 0);
+    return vdmc_graph_create_grouped(n, m, src, dst, ptrs_on_device, stream, out, nullptr, 0, 0u);
+}
+
+extern "C" vdmc_status vdmc_graph_create_ex(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                            int ptrs_on_device, uint32_t options, void *stream, vdmc_graph **out) {
+    if (options & ~(uint32_t)VDMC_GRAPH_UNDIRECTED) {
+        if (out) *out = nullptr;
+        return VDMC_ERR_INVALID_ARG;
+    }
+    return vdmc_graph_create_grouped(n, m, src, dst, ptrs_on_device, stream, out, nullptr, 0, options);
 }
 
 // goff: device int64[ngroups + 1] vertex offsets of the graphs of a batch,
 // or nullptr for a single graph
 vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                       int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
-                                      int32_t ngroups) {
+                                      int32_t ngroups, uint32_t options) {
     if (!out) return VDMC_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 0 || n >= (1 << 30) || m < 0 || m > 0xffffffffll) return VDMC_ERR_INVALID_ARG;
@@ -405,7 +428,7 @@ vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, 
     if (!g) return VDMC_ERR_OOM;
     std::memset(g, 0, sizeof *g);
     cudaStream_t s = (cudaStream_t)stream;
-    vdmc_status st = create_impl(n, m, src, dst, ptrs_on_device, s, g, goff, ngroups);
+    vdmc_status st = create_impl(n, m, src, dst, ptrs_on_device, s, g, goff, ngroups, options);
     if (st != VDMC_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -425,7 +448,6 @@ extern "C" vdmc_status vdmc_graph_destroy(vdmc_graph *g) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(g->device);
-    cudaDeviceSynchronize();
     free_graph_buffers(g);
     cudaSetDevice(cur);
     delete g;

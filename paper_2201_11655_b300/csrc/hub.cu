@@ -66,7 +66,11 @@ struct HubArgs {
     Csr g;
     const int32_t *new2old;
     uint64_t *out;
-    unsigned long long *d3;  // k = 4: n * VDMC_D3_COLS depth-3 credits (rank space)
+    // k = 4: depth-3 credits (rank space), n * VDMC_D3_COLS counters kept as
+    // 32-bit low words (d3lo) and high words (d3hi, touched only on a carry):
+    // the low words of a 1M-vertex graph (64 MB) stay in L2
+    uint32_t *d3lo, *d3hi;
+    unsigned long long *stats;  // [1] sets of hub roots, [2] of those visited one by one (or nullptr)
     const uint8_t *lut_g;
     const int32_t *hubs;
     int32_t nhubs;
@@ -262,6 +266,9 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
     }
     for (int i = tid; i < A.pbits_words; i += HUB_THREADS) pbits[i] = 0u;
     for (int i = tid; i < HUB_WARPS * C; i += HUB_THREADS) (&whist[0][0])[i] = 0ull;
+    // sets this thread visited one at a time (the enumerated exceptions of
+    // the signature counting); summed into stats[2] when the queue is empty
+    unsigned long long nenum = 0ull;
 
     for (;;) {
         __syncthreads();
@@ -295,7 +302,13 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
         if (tid < 3) ncol[tid] = 0u;
         __syncthreads();
         const int32_t r = s_root;
-        if (r < 0) break;
+        if (r < 0) {
+            if (A.stats) {
+                nenum = warp_sum(nenum);
+                if (lane == 0 && nenum) atomicAdd(A.stats + 2, nenum);
+            }
+            break;
+        }
         // part `part` of `nparts` of a split root: P members i with
         // i % nparts == part and Q vertices b with b % nparts == part
         const int32_t part = s_part >= 0 ? s_part : 0, nparts = s_part >= 0 ? A.split : 1;
@@ -624,6 +637,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                     const uint32_t cls = lut[mask3(al, cu, eu & 3u)];
                     sadd(hvh, cls, 1ull);
                     sadd(hP, cls, 1ull);
+                    nenum += (uint32_t)i < (eu >> 2) ? 1ull : 0ull;  // visited from both members
                 }
             } else {
                 // -- S1 per-member counts: H-edges inside R_v = P \ N_H[v] by type,
@@ -791,6 +805,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         // pair out of the bulk counts
                         const uint32_t cle = lut[mask4(al, cuo, 0u, fvo, fvc, fuc)];
                         const uint32_t clb = lut[mask4(al, cuo, 0u, 0u, fvc, fuc)];
+                        nenum++;
                         sadd(hvh, cle, 1ull);
                         gadd(S, uo, cle, 1ull, C);
                         gadd(S, c, cle, 1ull, C);
@@ -826,6 +841,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                             gadd(S, __ldg(P + yp) >> 2, cls, 1ull, C);
                             gadd(S, __ldg(P + zp) >> 2, cls, 1ull, C);
                             sadd(hP, cls, 3ull);
+                            nenum++;
                         }
                         j2 += 32;
                         while (j1 < dH - 1 && j2 >= dH) {
@@ -1118,6 +1134,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         const uint32_t clA = lut[mask4(cv, 0u, 0u, fvb, 0u, gg)];
                         const uint32_t clB = lut[mask4(cv, 0u, 0u, fvc, 0u, swapf(gg))];
                         const uint32_t who[3] = {vv, bo, c};
+                        nenum++;
 #pragma unroll
                         for (int m3 = 0; m3 < 3; m3++) {
                             gadd(S, who[m3], clE, 1ull, C);
@@ -1150,9 +1167,12 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         if (nzo && in_bounds(g, c < (uint32_t)g.n && gg != 0u)) {
 #pragma unroll
                             for (int k = 0; k < 9; k++)
-                                if ((nzo >> k) & 1u)
-                                    atomicAdd(A.d3 + (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1],
-                                              (unsigned long long)sq[w * 9 + k]);
+                                if ((nzo >> k) & 1u) {
+                                    const int64_t di = (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1];
+                                    const uint32_t v = sq[w * 9 + k];
+                                    const uint32_t old = atomicAdd(A.d3lo + di, v);
+                                    if ((uint32_t)(old + v) < old) atomicAdd(A.d3hi + di, 1u);  // carry
+                                }
                         }
                         cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
                     }
@@ -1187,11 +1207,17 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
             // S1 sets are counted once per member of P: a split root's parts
             // sum their partials, divided after the kernel (split_finish)
             unsigned long long *acc = nparts > 1 ? A.split_acc + (int64_t)s_esplit * C : nullptr;
+            unsigned long long tot = 0ull;  // sets of this root credited here
             for (int c = tid; c < C; c += HUB_THREADS) {
                 const unsigned long long p1 = hget(hP, c), d1 = hget(hD, c);
                 const unsigned long long v = (nparts == 1 ? p1 / (K == 3 ? 2ull : 3ull) : 0ull) + d1;
                 if (nparts > 1 && p1) atomicAdd(acc + c, p1);
                 if (v && ok) atomicAdd(out_r + c, v);
+                tot += v;
+            }
+            if (A.stats) {
+                tot = warp_sum(tot);
+                if (lane == 0 && tot) atomicAdd(A.stats + 1, tot);
             }
         }
         reset_slot<HUB_THREADS>(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
@@ -1201,15 +1227,19 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
 // root credit of the three-member sets of split roots: the parts' summed
 // partials / |P-members per set| (2 for k = 3, 3 for k = 4); one block per root
 __global__ void split_finish(const unsigned long long *__restrict__ acc, const int32_t *__restrict__ hubs,
-                             int32_t nsplit, int C, unsigned long long times, int64_t n, uint64_t *out) {
+                             int32_t nsplit, int C, unsigned long long times, int64_t n, uint64_t *out,
+                             unsigned long long *stats) {
     const int32_t e = blockIdx.x;
     if (e >= nsplit) return;
     const int32_t r = hubs[e];
     if (r < 0 || r >= n) return;
+    unsigned long long tot = 0ull;
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         const unsigned long long v = acc[(int64_t)e * C + c] / times;
         if (v) atomicAdd((unsigned long long *)&out[(int64_t)r * C + c], v);
+        tot += v;
     }
+    if (stats && tot) atomicAdd(stats + 1, tot);
 }
 
 __global__ void fill_i32(int32_t *p, int64_t n, int32_t v) {
@@ -1265,11 +1295,11 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-void vdmc_hub_free(vdmc_graph *g) {
-    cudaFree(g->hubs);
-    cudaFree(g->hub_scratch);
-    cudaFree(g->hub_qhead);
-    cudaFree(g->hub_split_buf);
+void vdmc_hub_free(vdmc_graph *g, cudaStream_t s) {
+    vdmc_free(g->hubs, s);
+    vdmc_free(g->hub_scratch, s);
+    vdmc_free(g->hub_qhead, s);
+    vdmc_free(g->hub_split_buf, s);
     g->hub_split_buf = nullptr;
     g->hub_split_cap = 0;
     g->hubs = nullptr;
@@ -1281,7 +1311,7 @@ void vdmc_hub_free(vdmc_graph *g) {
 }
 
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
-    vdmc_hub_free(g);
+    vdmc_hub_free(g, s);
     g->hub_min_l = min_l;
     const int32_t n = g->n;
     if (min_l <= 0 || n == 0) return VDMC_OK;
@@ -1299,7 +1329,7 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nh, pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && nh > 0) {
-        e = cudaMalloc((void **)&g->hubs, sizeof(int32_t) * nh);
+        e = vdmc_malloc(&g->hubs, sizeof(int32_t) * nh, s);
         if (e == cudaSuccess) {
             hub_compact<<<(n + 255) / 256, 256, 0, s>>>(flag, pos, n, g->hubs);
             e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 3, s);
@@ -1375,11 +1405,10 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     const int64_t queue = (int64_t)g->nhubs + (int64_t)nsplit * (split - 1);
     const size_t split_bytes = (size_t)nsplit * sizeof(unsigned long long) * C;
     if (nsplit > g->hub_split_cap) {
-        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(g->hub_split_buf);
+        vdmc_free(g->hub_split_buf, s);
         g->hub_split_buf = nullptr;
         g->hub_split_cap = 0;
-        VDMC_CUDA_TRY(cudaMalloc(&g->hub_split_buf, (size_t)nsplit * sizeof(unsigned long long) * 199));
+        VDMC_CUDA_TRY(vdmc_malloc(&g->hub_split_buf, (size_t)nsplit * sizeof(unsigned long long) * 199, s));
         g->hub_split_cap = nsplit;
     }
     if (nsplit > 0) VDMC_CUDA_TRY(cudaMemsetAsync(g->hub_split_buf, 0, split_bytes, s));
@@ -1387,13 +1416,12 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     slots = (int)std::min<int64_t>(slots, queue);
     if (slots > g->hub_slots) {
         // (re)allocate the per-slot scratch; posmap starts at -1, counters at 0
-        VDMC_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(g->hub_scratch);
+        vdmc_free(g->hub_scratch, s);
         g->hub_scratch = nullptr;
         g->hub_slots = 0;
         HubLayout L = hub_layout(g, slots);
-        VDMC_CUDA_TRY(cudaMalloc(&g->hub_scratch, L.total));
-        if (!g->hub_qhead) VDMC_CUDA_TRY(cudaMalloc((void **)&g->hub_qhead, sizeof(unsigned long long)));
+        VDMC_CUDA_TRY(vdmc_malloc(&g->hub_scratch, L.total, s));
+        if (!g->hub_qhead) VDMC_CUDA_TRY(vdmc_malloc(&g->hub_qhead, sizeof(unsigned long long), s));
         char *base = (char *)g->hub_scratch;
         VDMC_CUDA_TRY(cudaMemsetAsync(base + L.qcnt, 0, L.wq - L.qcnt, s));
         VDMC_CUDA_TRY(cudaMemsetAsync(base + L.tbits, 0, L.total - L.tbits, s));
@@ -1411,7 +1439,9 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     A.g = Csr{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
     A.new2old = nullptr;  // credits in rank space (see vdmc_count_internal)
     A.out = out;
-    A.d3 = (unsigned long long *)d3;
+    A.d3lo = reinterpret_cast<uint32_t *>(d3);
+    A.d3hi = d3 ? reinterpret_cast<uint32_t *>(d3) + (size_t)g->n * VDMC_D3_COLS : nullptr;
+    A.stats = g->stats;
     A.lut_g = lut;
     A.hubs = g->hubs;
     A.nhubs = g->nhubs;
@@ -1446,7 +1476,8 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     else le = warps == 32 ? launch_hub<4, 32>(slots, dsmem, A, s) : launch_hub<4, 16>(slots, dsmem, A, s);
     VDMC_CUDA_TRY(le);
     if (nsplit > 0) {
-        split_finish<<<(unsigned)nsplit, 256, 0, s>>>(A.split_acc, g->hubs, nsplit, C, k == 3 ? 2ull : 3ull, g->n, out);
+        split_finish<<<(unsigned)nsplit, 256, 0, s>>>(A.split_acc, g->hubs, nsplit, C, k == 3 ? 2ull : 3ull, g->n, out,
+                                                      g->stats);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     return VDMC_OK;

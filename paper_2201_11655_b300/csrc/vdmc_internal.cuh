@@ -58,20 +58,55 @@ struct vdmc_graph {
     unsigned long long *hub_qhead;
     void *hub_split_buf;         // split roots: nsplit * (C_k partial sums + a ticket)
     int32_t hub_split_cap;
-    cudaStream_t side;           // second stream: the two kernels overlap
+    cudaStream_t side;           // second stream: the two kernels overlap; also frees the graph
     cudaEvent_t ev_fork, ev_join;
+    cudaEvent_t ev_done;         // recorded after the graph's last build or count step
     uint64_t serial;             // creation number (identifies the graph in cached batch plans)
     int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
     uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
-    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * VDMC_D3_COLS (rank space)
+    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel: n * VDMC_D3_COLS
+                                 // low 32-bit words, then as many high words (rank space)
+    unsigned long long *stats;   // VDMC_NSTATS counters of the last count (vdmc_count_stats)
+    int undirected;              // VDMC_GRAPH_UNDIRECTED: every edge carries flags 3, output in undirected classes
+    // per-edge counts (vdmc_count_edges), built on first use
+    int64_t *ebase;              // n + 1: the edges of rank r's upper row have ids ebase[r] .. ebase[r+1]-1
+    int64_t *erow;               // edge id -> output row (edges in (min, max) original-id order)
+    uint64_t *ekeys;             // output row -> (min original id << 30) | max original id
+    uint8_t *eflags;             // output row -> bit 0: arc min -> max, bit 1: arc max -> min
+    Task *etasks;                // every root, for the per-edge kernel
+    int64_t netasks;
+    int32_t etasks_a_chunk;
 };
+
+// Counters of one count, reset at its start (vdmc_count_stats_t):
+//   [0] sets the warp-per-task kernel enumerated one by one
+//   [1] sets rooted at roots of the root-per-CTA kernel (all of its sets)
+//   [2] of those, sets that kernel visited one at a time (the rest are
+//       accounted for by signature formulas)
+constexpr int VDMC_NSTATS = 4;
 
 // Depth-3 credit columns per vertex (k = 4, root-per-CTA kernel): the paths
 // r - x - b - c credited to c are typed by (colour of x, h(x, b), h(b, c)),
 // 27 types in 15 classes (a path and its reverse are isomorphic); one column
 // per class, 16 columns = one 128-byte line per vertex.
 constexpr int VDMC_D3_COLS = 16;
+
+// ---- device memory ----
+// Graph-owned device memory is stream-ordered (cudaMallocAsync on the stream
+// of the call that needs it, cudaFreeAsync when the graph is destroyed), so
+// creating, counting or destroying one graph never waits for the work of
+// other graphs on other streams.
+inline cudaError_t vdmc_malloc(void **p, size_t bytes, cudaStream_t s) {
+    return cudaMallocAsync(p, bytes ? bytes : 1, s);
+}
+template <typename T>
+inline cudaError_t vdmc_malloc(T **p, size_t bytes, cudaStream_t s) {
+    return vdmc_malloc(reinterpret_cast<void **>(p), bytes, s);
+}
+inline void vdmc_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
 
 // ---- status helpers ----
 #define VDMC_CUDA_TRY(expr)                                         \
@@ -100,15 +135,23 @@ cudaError_t vdmc_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t count, in
 // induced graph is not weakly connected.  Built once per k, host memory.
 const uint8_t *vdmc_host_lut(int k);
 const uint16_t *vdmc_host_canon(int k, int *num_classes);
+// undirected variant: column of each directed class among the symmetric ones
+// (255 = not symmetric), and their number (2 for k = 3, 6 for k = 4)
+const uint8_t *vdmc_host_ucol(int k, int *num_undirected);
 
 // ---- counting (count.cu) ----
 vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s);
 cudaError_t vdmc_device_lut(int k, const uint8_t **out);
+cudaError_t vdmc_device_ucol(int k, const uint8_t **out);
+
+// ---- per-edge counts (edges.cu) ----
+// builds g->ebase, g->erow, g->ekeys, g->eflags on first use (on stream s)
+vdmc_status vdmc_edge_index(vdmc_graph *g, cudaStream_t s);
 
 // ---- graph build (graph_build.cu) ----
 vdmc_status vdmc_graph_create_grouped(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                       int ptrs_on_device, void *stream, vdmc_graph **out, const int64_t *goff,
-                                      int32_t ngroups);
+                                      int32_t ngroups, uint32_t options);
 
 // ---- batch plans (batch.cu) ----
 void vdmc_batch_plan_free(vdmc_graph *g);
@@ -124,4 +167,4 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
 vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
                             int32_t hi, int blocks_per_sm, int split, int split_roots, int warps,
                             cudaStream_t s);
-void vdmc_hub_free(vdmc_graph *g);
+void vdmc_hub_free(vdmc_graph *g, cudaStream_t s);

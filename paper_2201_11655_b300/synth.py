@@ -216,9 +216,12 @@ WORKLOADS = {
     # expected degree 20k, reciprocity 0.2.
     "chunglu_n1M_m10M_a2.3_r0.2": lambda seed=2: chung_lu(
         1_000_000, 10.0 / 1.2, 2.3, seed, reciprocity=0.2, max_degree=20_000),
-    # The same power-law shape at 1/10 scale (profiling captures).
+    # The same power-law shape at 1/10 and 3/10 scale (profiling captures;
+    # the cap on the expected degree scales with sqrt(n)).
     "chunglu_n100k_m1M_a2.3_r0.2": lambda seed=2: chung_lu(
         100_000, 10.0 / 1.2, 2.3, seed, reciprocity=0.2, max_degree=6_000),
+    "chunglu_n300k_m3M_a2.3_r0.2": lambda seed=2: chung_lu(
+        300_000, 10.0 / 1.2, 2.3, seed, reciprocity=0.2, max_degree=11_000),
     # Directed uniform-endpoint ER, 4M vertices, 32M arcs.
     "er_n4M_m32M": lambda seed=3: er_uniform(4_000_000, 32_000_000, seed),
 }

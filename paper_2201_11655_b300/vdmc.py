@@ -47,6 +47,24 @@ class Schedule(ctypes.Structure):
                 ("hub_blocks_per_sm", ctypes.c_int32), ("hub_split", ctypes.c_int32),
                 ("hub_split_roots", ctypes.c_int32), ("hub_warps", ctypes.c_int32)]
 
+
+class WorkModel(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "bytes", "bytes_per_use", "entries_root", "entries_depth1", "entries_depth2", "entries_depth2_per_use",
+        "output_bytes")]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class CountStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "sets_plain", "sets_hub", "sets_hub_enumerated", "sets_by_signature", "sets_enumerated")]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 SCHEDULE_KEYS = ("a_chunk", "warps_per_block", "blocks_per_sm", "hub_min_l", "hub_blocks_per_sm", "hub_split",
                  "hub_split_roots", "hub_warps")
 
@@ -63,6 +81,13 @@ def _lib():
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         sig = {
             "vdmc_graph_create": ([i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+            "vdmc_graph_create_ex": ([i32, i64, vp, vp, ctypes.c_int, ctypes.c_uint32, vp, ctypes.POINTER(vp)],
+                                     ctypes.c_int),
+            "vdmc_num_classes_undirected": ([ctypes.c_int], ctypes.c_int),
+            "vdmc_undirected_class_masks": ([ctypes.c_int, vp], ctypes.c_int),
+            "vdmc_graph_num_classes": ([vp, ctypes.c_int], ctypes.c_int),
+            "vdmc_count_edges": ([vp, ctypes.c_int, vp, vp], ctypes.c_int),
+            "vdmc_graph_edges": ([vp, vp, vp, vp], ctypes.c_int),
             "vdmc_graph_destroy": ([vp], ctypes.c_int),
             "vdmc_graph_create_batch": ([ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)],
                                         ctypes.c_int),
@@ -77,6 +102,9 @@ def _lib():
             "vdmc_count_batch": ([vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
             "vdmc_get_device_status": ([vp], ctypes.c_int),
             "vdmc_work_bytes": ([vp, ctypes.c_int, vp], ctypes.c_int),
+            "vdmc_work_model": ([vp, ctypes.c_int, ctypes.POINTER(WorkModel)], ctypes.c_int),
+            "vdmc_count_stats": ([vp, ctypes.POINTER(CountStats)], ctypes.c_int),
+            "vdmc_root_costs": ([vp, ctypes.c_int, vp, vp], ctypes.c_int),
             "vdmc_set_schedule": ([ctypes.POINTER(Schedule)], ctypes.c_int),
             "vdmc_get_schedule": ([ctypes.POINTER(Schedule)], ctypes.c_int),
             "vdmc_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -121,6 +149,19 @@ def class_masks(k: int) -> np.ndarray:
     return out
 
 
+def num_classes_undirected(k: int) -> int:
+    return _lib().vdmc_num_classes_undirected(k)
+
+
+def undirected_class_masks(k: int) -> np.ndarray:
+    nc = num_classes_undirected(k)
+    if nc < 0:
+        raise ValueError("k must be 3 or 4")
+    out = np.zeros(nc, np.uint16)
+    _check(_lib().vdmc_undirected_class_masks(k, out.ctypes.data), "vdmc_undirected_class_masks")
+    return out
+
+
 def class_lut(k: int) -> np.ndarray:
     """Output column of every motif index (255 = not weakly connected)."""
     if k not in (3, 4):
@@ -133,9 +174,26 @@ def class_lut(k: int) -> np.ndarray:
 class Graph:
     """A device graph built by ``vdmc_graph_create``; freed by ``close()``."""
 
-    def __init__(self, handle, n):
+    def __init__(self, handle, n, undirected=False):
         self._h = handle
         self.n = n
+        self.undirected = undirected
+
+    def num_classes(self, k: int) -> int:
+        """Columns of this graph's counts (directed or undirected classes)."""
+        nc = _lib().vdmc_graph_num_classes(self.handle, int(k))
+        if nc < 0:
+            raise ValueError("k must be 3 or 4")
+        return nc
+
+    def edges(self):
+        """(u, v, flags) of the rows of per-edge counts: u < v original ids, ascending."""
+        ne = self.info()["edges_u"]
+        u = np.zeros(ne, np.int32)
+        v = np.zeros(ne, np.int32)
+        f = np.zeros(ne, np.uint8)
+        _check(_lib().vdmc_graph_edges(self.handle, u.ctypes.data, v.ctypes.data, f.ctypes.data), "vdmc_graph_edges")
+        return u, v, f
 
     @property
     def handle(self):
@@ -163,6 +221,18 @@ class Graph:
         _check(_lib().vdmc_work_bytes(self.handle, int(k), b.ctypes.data), "vdmc_work_bytes")
         return int(b[0])
 
+    def work_model(self, k: int) -> dict:
+        """The algorithmic byte model of one count (vdmc_work_model_t as a dict)."""
+        m = WorkModel()
+        _check(_lib().vdmc_work_model(self.handle, int(k), ctypes.byref(m)), "vdmc_work_model")
+        return m.as_dict()
+
+    def count_stats(self) -> dict:
+        """Sets found one by one vs by signature in the last count (vdmc_count_stats_t)."""
+        st = CountStats()
+        _check(_lib().vdmc_count_stats(self.handle, ctypes.byref(st)), "vdmc_count_stats")
+        return st.as_dict()
+
     def device_status(self) -> int:
         return _lib().vdmc_get_device_status(self.handle)
 
@@ -184,8 +254,10 @@ class Graph:
         self.close()
 
 
-def graph_create(n: int, src, dst, stream=None) -> Graph:
-    """Build a graph from arcs src[e] -> dst[e] (int32; numpy/CPU tensors or CUDA tensors)."""
+def graph_create(n: int, src, dst, stream=None, undirected: bool = False) -> Graph:
+    """Build a graph from arcs src[e] -> dst[e] (int32; numpy/CPU tensors or CUDA tensors).
+
+    undirected=True: count the undirected motifs of G_U (arc directions ignored)."""
     import torch
     lib = _lib()
     on_device = 0
@@ -204,9 +276,10 @@ def graph_create(n: int, src, dst, stream=None) -> Graph:
     if (d.numel() if on_device else d.size) != m:
         raise ValueError("src and dst differ in length")
     h = ctypes.c_void_p()
-    _check(lib.vdmc_graph_create(int(n), int(m), ctypes.c_void_p(ps), ctypes.c_void_p(pd), on_device,
-                                 _stream_ptr(stream), ctypes.byref(h)), "vdmc_graph_create")
-    return Graph(h, int(n))
+    _check(lib.vdmc_graph_create_ex(int(n), int(m), ctypes.c_void_p(ps), ctypes.c_void_p(pd), on_device,
+                                    1 if undirected else 0, _stream_ptr(stream), ctypes.byref(h)),
+           "vdmc_graph_create_ex")
+    return Graph(h, int(n), undirected)
 
 
 def graph_create_batch(graphs, stream=None) -> Graph:
@@ -230,15 +303,16 @@ def graph_create_batch(graphs, stream=None) -> Graph:
     return g
 
 
-def _out_tensor(g: Graph, k: int, out):
+def _out_tensor(g: Graph, k: int, out, rows=None):
     import torch
-    nc = num_classes(k)
-    if nc < 0:
+    if k not in (3, 4):
         raise ValueError("k must be 3 or 4")
+    nc = g.num_classes(k)
+    rows = g.n if rows is None else rows
     if out is None:
-        out = torch.empty((g.n, nc), dtype=torch.uint64, device="cuda")
-    if out.dtype != torch.uint64 or not out.is_cuda or out.numel() != g.n * nc or not out.is_contiguous():
-        raise ValueError("out must be a contiguous CUDA uint64 tensor of n*C_k elements")
+        out = torch.empty((rows, nc), dtype=torch.uint64, device="cuda")
+    if out.dtype != torch.uint64 or not out.is_cuda or out.numel() != rows * nc or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA uint64 tensor of %d x %d elements" % (rows, nc))
     return out
 
 
@@ -246,6 +320,14 @@ def count(g: Graph, k: int, out=None, stream=None):
     """Per-vertex counts, uint64[n, C_k] CUDA tensor (overwritten)."""
     out = _out_tensor(g, k, out)
     _check(_lib().vdmc_count(g.handle, int(k), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "vdmc_count")
+    return out
+
+
+def count_edges(g: Graph, k: int, out=None, stream=None):
+    """Per-edge counts, uint64[edges_u, columns] CUDA tensor (rows: Graph.edges() order)."""
+    out = _out_tensor(g, k, out, rows=g.info()["edges_u"])
+    _check(_lib().vdmc_count_edges(g.handle, int(k), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "vdmc_count_edges")
     return out
 
 

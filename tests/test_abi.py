@@ -90,3 +90,13 @@ def test_schedule_roundtrip(lib):
                 vdmc.set_schedule(**bad)
     finally:
         vdmc.set_schedule(**old)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_undirected_class_tables_match_oracle(lib, k):
+    # the library keeps the directed classes of symmetric matrices; the
+    # oracle enumerates symmetric connected matrices directly
+    canon, _ = O.classes_undirected(k)
+    assert vdmc.num_classes_undirected(k) == len(canon)
+    np.testing.assert_array_equal(vdmc.undirected_class_masks(k).astype(np.int64), canon)
+    assert vdmc.num_classes_undirected(5) == -1

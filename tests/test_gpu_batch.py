@@ -46,6 +46,33 @@ def test_union_matches_oracle_per_graph(k):
         np.testing.assert_array_equal(out[off[i]:off[i + 1]], want, err_msg="graph %d" % i)
 
 
+def test_union_700_graphs_full_recipe_vs_oracle():
+    # 700 graphs drawn from the batch workload's own recipe (n log-uniform in
+    # [10, 500], half G(n,p), half Chung-Lu 2.5, p ~ U[0.02, 0.2]), counted in
+    # one launch per k: every graph against the oracle at k=3, and at k=4 the
+    # graphs the oracle can count in seconds (its own k=3 set count <= 10^5;
+    # at least 500 of them)
+    from paper_2201_11655_b300 import vdmc
+    graphs = synth.batch(700, 21)
+    with vdmc.graph_create_batch(graphs) as U:
+        out3 = to_numpy_u64(vdmc.count(U, 3))
+        out4 = to_numpy_u64(vdmc.count(U, 4))
+        torch.cuda.synchronize()
+        assert U.device_status() == 0
+    off = U.offsets
+    small = []
+    for i, (n, s, d) in enumerate(graphs):
+        want, found = O.count(n, s, d, 3)
+        np.testing.assert_array_equal(out3[off[i]:off[i + 1]], want, err_msg="k=3 graph %d" % i)
+        if found <= 100_000:
+            small.append(i)
+    assert len(small) >= 500
+    for i in small:
+        n, s, d = graphs[i]
+        want, _ = O.count(n, s, d, 4)
+        np.testing.assert_array_equal(out4[off[i]:off[i + 1]], want, err_msg="k=4 graph %d" % i)
+
+
 def test_union_with_hub_kernel_matches_plain_per_graph():
     from paper_2201_11655_b300 import vdmc
     graphs = small_batch(300, 9, n_hi=500)

@@ -1,14 +1,23 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times.
 
 The oracle cannot count the full graphs, so it checks sampled root ranges
-(every set whose lowest-rank member lies in the range, by Lemma 1) across the
-degree spectrum; the rest is checked by properties that hold at any size:
-ranges partition the full count, the two counting kernels agree on heavy
-roots, and the k=3 totals obey the degree/triangle identity.
+(every set whose lowest-rank member lies in the range, by Lemma 1): the
+heaviest roots at k=3, a heavy root of the root-per-CTA kernel at k=4, and
+ranges stratified over the degree deciles.  The rest is checked by properties
+that hold at any size:
+  * transposing every arc permutes the classes (the class-transpose map is
+    taken from the oracle's canonical index), so count(G^T) must equal
+    count(G) with its columns permuted -- every hub root is counted again with
+    its colours swapped;
+  * relabelling the vertices permutes the rows (and reorders equal-degree
+    roots, so different roots take different kernel paths);
+  * disjoint rank ranges sum to the full count;
+  * the two counting kernels agree on split and unsplit heavy roots;
+  * the k=3 totals obey the degree/triangle identity.
+Range sizes are chosen by probing the set count on the device (a size, not an
+expected value); every expected value comes from the oracle or from the
+untransformed count.
 """
-import math
-import os
-
 import numpy as np
 import pytest
 
@@ -38,17 +47,107 @@ def rows_of(out):
     return nz.cpu().numpy(), o[nz].cpu().numpy().view(np.uint64), int(o.sum().item())
 
 
+def compare_rows(got, want, k, found, what):
+    ids, rows, total = rows_of(got)
+    wids = np.nonzero(want.sum(axis=1))[0]
+    np.testing.assert_array_equal(ids, wids, err_msg="k=%d %s: non-zero rows" % (k, what))
+    np.testing.assert_array_equal(rows, want[wids], err_msg="k=%d %s" % (k, what))
+    assert total == k * found
+
+
 def check_range(vdmc, g, n, s, d, k, rank, lo, hi):
     out = vdmc.count_roots(g, k, lo, hi)
     torch.cuda.synchronize()
     assert g.device_status() == 0
-    ids, rows, total = rows_of(out)
     want, found = O.count_roots(n, s, d, k, rank, lo, hi)
-    wids = np.nonzero(want.sum(axis=1))[0]
-    np.testing.assert_array_equal(ids, wids, err_msg="k=%d ranks [%d,%d)" % (k, lo, hi))
-    np.testing.assert_array_equal(rows, want[wids], err_msg="k=%d ranks [%d,%d)" % (k, lo, hi))
-    assert total == k * found
+    compare_rows(out, want, k, found, "ranks [%d,%d)" % (lo, hi))
     return found
+
+
+def check_ranges(vdmc, g, n, s, d, k, rank, ranges):
+    """Many disjoint rank ranges against one oracle call over all of them."""
+    acc = None
+    for lo, hi in ranges:
+        part = vdmc.count_roots(g, k, lo, hi).view(torch.int64)
+        acc = part.clone() if acc is None else acc.add_(part)
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    want, found = O.count_root_ranges(n, s, d, k, rank, ranges)
+    compare_rows(acc, want, k, found, "%d ranges" % len(ranges))
+    return found
+
+
+def sets_in(vdmc, g, k, lo, hi):
+    out = vdmc.count_roots(g, k, lo, hi)
+    return int(out.view(torch.int64).sum().item()) // k
+
+
+def stratified_ranges(vdmc, g, k, n, per_decile, budget, skip_heavy=0):
+    """per_decile ranges in each tenth of the rank space, each grown (by
+    doubling from one root) while its set count stays within budget; a start
+    whose single root exceeds the budget moves to a lighter rank."""
+    ranges = []
+    for dec in range(10):
+        for i in range(per_decile):
+            lo = dec * n // 10 + i * n // (10 * per_decile)
+            lo = max(lo, skip_heavy)
+            while lo < n - 1 and sets_in(vdmc, g, k, lo, lo + 1) > budget:
+                lo = lo * 2 + 1
+            if lo >= n:
+                continue
+            w = 1
+            while lo + 2 * w <= n and w < 4096 and sets_in(vdmc, g, k, lo, lo + 2 * w) <= budget:
+                w *= 2
+            if not ranges or lo >= ranges[-1][1]:
+                ranges.append((lo, min(n, lo + w)))
+    return ranges
+
+
+def class_transpose_map(k):
+    """tau[c] = column of the class of the transposed motif of column c (oracle tables)."""
+    canon, _ = O.classes(k)
+    col = {int(m): i for i, m in enumerate(canon)}
+    nb = k * (k - 1)
+    tau = []
+    for m in canon:
+        bits = [(int(m) >> (nb - 1 - p)) & 1 for p in range(nb)]
+        adj = np.zeros((k, k), int)
+        p = 0
+        for i in range(k):
+            for j in range(k):
+                if i != j:
+                    adj[i, j] = bits[p]
+                    p += 1
+        t = adj.T
+        idx = 0
+        for i in range(k):
+            for j in range(k):
+                if i != j:
+                    idx = (idx << 1) | int(t[i, j])
+        tau.append(col[O.canonical_index(k, idx)])
+    return np.array(tau)
+
+
+def check_transpose(vdmc, n, s, d, k, out):
+    """count(G^T)[:, tau[c]] == count(G)[:, c] for every column c."""
+    tau = torch.from_numpy(class_transpose_map(k)).cuda()
+    with vdmc.graph_create(n, torch.from_numpy(d).cuda(), torch.from_numpy(s).cuda()) as gt:
+        ot = vdmc.count(gt, k).view(torch.int64)
+        torch.cuda.synchronize()
+        assert gt.device_status() == 0
+        assert torch.equal(ot[:, tau], out.view(torch.int64)), "k=%d transpose" % k
+
+
+def check_relabel(vdmc, n, s, d, k, out, seed):
+    """count(pi(G))[pi(v)] == count(G)[v] for a random relabelling pi."""
+    perm = np.random.default_rng(seed).permutation(n).astype(np.int32)
+    ps = torch.from_numpy(perm[s]).cuda()
+    pd = torch.from_numpy(perm[d]).cuda()
+    with vdmc.graph_create(n, ps, pd) as gp:
+        op = vdmc.count(gp, k).view(torch.int64)
+        torch.cuda.synchronize()
+        assert gp.device_status() == 0
+        assert torch.equal(op[torch.from_numpy(perm).long().cuda()], out.view(torch.int64)), "k=%d relabel" % k
 
 
 @pytest.fixture(scope="module")
@@ -62,19 +161,38 @@ def powerlaw(env):
     g.close()
 
 
-def test_powerlaw_root_samples_vs_oracle(powerlaw):
+def test_powerlaw_heaviest_roots_k3_vs_oracle(powerlaw):
+    # rank 0 (17,018 higher-rank neighbours, ~1.5e8 sets) and ranks 31, 32:
+    # the last split root and the first unsplit root of the tuned schedule
     vdmc, g, n, s, d, rank = powerlaw
-    info = g.info()
-    assert info["num_hub_roots"] > 0
-    # Root samples across the degree spectrum, each small enough for the
-    # oracle (it runs one root per thread; the heaviest roots hold ~10^12
-    # 4-sets and are checked below by kernel agreement and partitions).
-    for lo, hi in ((5000, 5100), (60_000, 61_000), (700_000, 720_000)):
-        check_range(vdmc, g, n, s, d, 3, rank, lo, hi)
-    # k=4: roots of the root-per-CTA kernel (L >= 32 under the tuned
-    # schedule) and of the warp-per-task kernel
-    for lo, hi in ((8000, 8010), (20_000, 20_100), (200_000, 203_000)):
-        check_range(vdmc, g, n, s, d, 4, rank, lo, hi)
+    assert g.info()["num_hub_roots"] > 0
+    assert vdmc.get_schedule()["hub_split_roots"] >= 32
+    check_range(vdmc, g, n, s, d, 3, rank, 0, 1)
+    check_range(vdmc, g, n, s, d, 3, rank, 31, 33)
+
+
+def test_powerlaw_hub_root_k4_vs_oracle(powerlaw):
+    # rank 1000: 640 higher-rank neighbours, ~7e7 sets, root-per-CTA kernel
+    vdmc, g, n, s, d, rank = powerlaw
+    check_range(vdmc, g, n, s, d, 4, rank, 1000, 1001)
+
+
+@pytest.mark.parametrize("k,budget", [(3, 2_000_000), (4, 2_000_000)])
+def test_powerlaw_stratified_ranges_vs_oracle(powerlaw, k, budget):
+    vdmc, g, n, s, d, rank = powerlaw
+    ranges = stratified_ranges(vdmc, g, k, n, per_decile=5, budget=budget, skip_heavy=2000 if k == 4 else 0)
+    assert len(ranges) >= 50
+    check_ranges(vdmc, g, n, s, d, k, rank, ranges)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_powerlaw_transpose_and_relabel(powerlaw, k):
+    vdmc, g, n, s, d, rank = powerlaw
+    out = vdmc.count(g, k)
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    check_transpose(vdmc, n, s, d, k, out)
+    check_relabel(vdmc, n, s, d, k, out, seed=11 + k)
 
 
 def test_powerlaw_partition_and_kernel_agreement(powerlaw):
@@ -85,15 +203,18 @@ def test_powerlaw_partition_and_kernel_agreement(powerlaw):
         acc += vdmc.count_roots(g, 4, lo, hi).view(torch.int64)
     torch.cuda.synchronize()
     assert torch.equal(acc, full.view(torch.int64))
-    # heavy roots through each kernel
+    # heavy roots through each kernel: rank 31 (a split root under the tuned
+    # schedule), rank 32 (the first unsplit one), rank 300
     old = vdmc.get_schedule()
     try:
-        vdmc.set_schedule(hub_min_l=1)
-        a = vdmc.count_roots(g, 4, 2000, 2003).view(torch.int64).clone()
-        vdmc.set_schedule(hub_min_l=0)
-        b = vdmc.count_roots(g, 4, 2000, 2003).view(torch.int64).clone()
-        torch.cuda.synchronize()
-        assert int(a.sum()) > 0 and torch.equal(a, b)
+        for lo, hi in ((31, 32), (32, 33), (300, 301)):
+            vdmc.set_schedule(hub_min_l=1)
+            a = vdmc.count_roots(g, 4, lo, hi).view(torch.int64).clone()
+            vdmc.set_schedule(hub_min_l=0)
+            b = vdmc.count_roots(g, 4, lo, hi).view(torch.int64).clone()
+            torch.cuda.synchronize()
+            assert g.device_status() == 0
+            assert int(a.sum()) > 0 and torch.equal(a, b), "ranks [%d,%d)" % (lo, hi)
     finally:
         vdmc.set_schedule(**old)
 
@@ -120,17 +241,33 @@ def test_powerlaw_k3_degree_triangle_identity(powerlaw):
     np.testing.assert_array_equal(tot, deg_o * (deg_o - 1) // 2 + nbs_o - 2 * tri)
 
 
-def test_er4m_root_samples_vs_oracle(env):
+@pytest.fixture(scope="module")
+def er4m(env):
     vdmc, autotune = env
     n, s, d = synth.workload("er_n4M_m32M")
+    autotune.apply_tuned(4, n, len(s))
     g = vdmc.graph_create(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
     rank = O.degree_rank(n, s, d)
-    try:
-        check_range(vdmc, g, n, s, d, 4, rank, 0, 400)
-        full = vdmc.count(g, 4).view(torch.int64)
-        part = vdmc.count_roots(g, 4, 0, 1_000_000).view(torch.int64) + \
-            vdmc.count_roots(g, 4, 1_000_000, n).view(torch.int64)
-        torch.cuda.synchronize()
-        assert torch.equal(full, part)
-    finally:
-        g.close()
+    yield vdmc, g, n, s, d, rank
+    g.close()
+
+
+def test_er4m_ranges_across_rank_space_vs_oracle(er4m):
+    # 25 ranges of 400 roots spread over the whole rank space, plus the
+    # highest-degree roots
+    vdmc, g, n, s, d, rank = er4m
+    ranges = [(0, 400)] + [(j * n // 25, j * n // 25 + 400) for j in range(1, 25)]
+    check_ranges(vdmc, g, n, s, d, 4, rank, ranges)
+
+
+def test_er4m_transpose_relabel_partition(er4m):
+    vdmc, g, n, s, d, rank = er4m
+    full = vdmc.count(g, 4)
+    torch.cuda.synchronize()
+    assert g.device_status() == 0
+    part = vdmc.count_roots(g, 4, 0, 1_000_000).view(torch.int64) + \
+        vdmc.count_roots(g, 4, 1_000_000, n).view(torch.int64)
+    torch.cuda.synchronize()
+    assert torch.equal(full.view(torch.int64), part)
+    check_transpose(vdmc, n, s, d, 4, full)
+    check_relabel(vdmc, n, s, d, 4, full, seed=5)

@@ -122,3 +122,30 @@ def test_failed_launch_reports_error_and_continues():
     done = drive(srv, clock)
     errs = {r.rid: r.error for r in done}
     assert errs[0] and errs[1] is None
+
+
+class FailingFinishBackend(FakeBackend):
+    """finish() raises for jobs holding a request of a given size (a device
+    status error, simulated on the host)."""
+
+    def __init__(self, clock, bad_n):
+        super().__init__(clock)
+        self.bad_n = bad_n
+
+    def finish(self, h):
+        if any(r.n == self.bad_n for r in h["reqs"]):
+            raise RuntimeError("device status 5")
+        return super().finish(h)
+
+
+def test_failed_job_does_not_stop_the_loop():
+    clock = Clock()
+    srv = Server(FailingFinishBackend(clock, bad_n=50_000), memory_budget=10 ** 12, max_inflight=2, small_n=1000,
+                 batch_max=4, batch_wait=1e-3, clock=clock)
+    reqs = [mk(i, 100 + i, 3, t=i * 1e-4) for i in range(12)] + [mk(99, 50_000, 4, t=2e-4)]
+    srv.submit_stream(reqs)
+    done = drive(srv, clock)
+    assert len(done) == len(reqs)
+    bad = [r for r in done if r.error]
+    assert [r.rid for r in bad] == [99] and "status" in bad[0].error
+    assert all(r.counts is not None for r in done if r.error is None)
