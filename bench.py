@@ -60,7 +60,7 @@ def parse():
                    help="graphs of the batch also counted one launch per graph")
     p.add_argument("--no-sub", action="store_true", help="skip the 4M-vertex ER and G(100, 0.08) sub-benchmarks")
     p.add_argument("--serve-requests", type=int, default=2000, help="requests per offered-load point")
-    p.add_argument("--serve-n-hi", type=int, default=100_000)
+    p.add_argument("--serve-n-hi", type=int, default=50_000)
     p.add_argument("--serve-loads", default="0.25,0.5,0.75,0.9", help="offered loads (fractions of capacity)")
     p.add_argument("--no-tuned", action="store_true", help="keep the library's default schedule")
     return p.parse_args()
@@ -81,31 +81,31 @@ def load_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the root-per-CTA kernel's sources (the kernel the traffic record covers)."""
     h = hashlib.sha256()
-    for name in ("hub.cu", "count.cu", "device_common.cuh", "vdmc_internal.cuh"):
+    for name in ("hub.cu", "device_common.cuh", "vdmc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2201_11655_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(k, full_alg_bytes):
-    """DRAM bytes per count, from a committed one-launch ncu record of a smaller
-    graph of the same shape (profiles/traffic_small_case.json), scaled to this
-    workload by its algorithmic bytes; None unless the record was taken on the
-    current kernel sources."""
+def load_traffic(k):
+    """The committed one-launch ncu record of the root-per-CTA kernel on a smaller
+    graph of the same shape (profiles/traffic_small_case.json), if it was taken
+    on the current kernel sources.  Its DRAM bytes are not scaled to the full
+    workload: the ratio to the algorithmic bytes grows with the graph (the
+    scratch of all slots outgrows L2), so `traffic` stays null and the record is
+    reported beside it."""
     path = os.path.join(ROOT, "profiles", "traffic_small_case.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         e = rec.get("k%d" % k)
         if e and e.get("kernel_hash") == kernel_source_hash():
-            ratio = e["dram_bytes_per_count"] / e["algorithmic_bytes"]
-            return int(ratio * full_alg_bytes), {"workload": e["workload"], "ratio_to_algorithmic": ratio,
-                                                 "dram_bytes": e["dram_bytes_per_count"],
-                                                 "algorithmic_bytes": e["algorithmic_bytes"]}
+            return dict(e, ratio_to_algorithmic=e["dram_bytes_per_launch"] / e["algorithmic_bytes_of_count"])
     except Exception:
         pass
-    return None, None
+    return None
 
 
 class Clocks:
@@ -228,18 +228,23 @@ def roofline_of(model, ms, peak, peak_kind, kernel, traffic=None, traffic_src=No
                            "frac": model["bytes_per_use"] / (ms / 1e3) / 1e9 / peak},
          "model": model}
     if traffic_src:
-        r["traffic_source"] = traffic_src
+        r["traffic_small_case"] = traffic_src
     return r
 
 
-def bench_single(name, k, peak, peak_kind, tuned=True, reps=3):
+def bench_single(name, k, peak, peak_kind, base_schedule, tuned=True, override=None, reps=3):
     """One named single-graph workload: device time per count, instances/s
-    (enumerated / by signature), algorithmic-byte roofline."""
+    (enumerated / by signature), algorithmic-byte roofline.  The schedule is
+    the library default (base_schedule), then the tuned entry of the graph's
+    size bucket if any, then `override`."""
     import torch
     from paper_2201_11655_b300 import autotune, synth, vdmc
     n, s, d = synth.workload(name)
     saved = vdmc.get_schedule()
+    vdmc.set_schedule(**base_schedule)
     sched = autotune.apply_tuned(k, n, len(s)) if tuned else None
+    if override:
+        vdmc.set_schedule(**override)
     g = vdmc.graph_create(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
     try:
         out = torch.empty((n, vdmc.num_classes(k)), dtype=torch.uint64, device="cuda")
@@ -257,7 +262,8 @@ def bench_single(name, k, peak, peak_kind, tuned=True, reps=3):
         model = g.work_model(k)
         res = {"workload": name, "k": k, "n": n, "arcs": int(len(s)), "ms_per_count": ms,
                "instances": inst, "instances_per_s": inst / (ms / 1e3),
-               "schedule": vdmc.get_schedule(), "schedule_source": "tuned" if sched else "default",
+               "schedule": vdmc.get_schedule(),
+               "schedule_source": ("tuned" if sched else "default") + ("+%s" % override if override else ""),
                "roofline": roofline_of(model, ms, peak, peak_kind, "vdmc_count (all kernels of one count)")}
         res.update(rates(stats, ms))
         return res
@@ -282,6 +288,7 @@ def bench_batch(args, ks=(3, 4)):
     for k in ks:
         C = vdmc.num_classes(k)
         saved = vdmc.get_schedule()
+        vdmc.set_schedule(**getattr(args, "base_schedule", saved))
         tuned = None if args.no_tuned else autotune.apply_tuned(k, sum(g[0] for g in graphs),
                                                                 sum(len(g[1]) for g in graphs))
         try:
@@ -378,6 +385,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     build.build()
     vdmc.load()
+    base_schedule = vdmc.get_schedule()  # the library default, before any tuned entry
     k = args.k
     C = vdmc.num_classes(k)
     n, s, d = synth.workload(args.workload)
@@ -471,11 +479,10 @@ def run_ours(args):
 
     peak, peak_kind = load_peaks()
     model = g.work_model(k)
-    traffic, traffic_src = load_traffic(k, model["bytes"])
     roofline = roofline_of(model, ms, peak, peak_kind,
                            "vdmc_count: hub_kernel<%d, %d warps> (root-per-CTA) overlapped with count_kernel<%d> "
                            "(warp-per-task), timed together" % (k, vdmc.get_schedule()["hub_warps"] or 16, k),
-                           traffic, traffic_src)
+                           None, load_traffic(k))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -490,10 +497,17 @@ def run_ours(args):
     g.close()
     extra = {}
     if rank == 0 and world == 1 and not args.no_sub:
-        extra["er4m"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, tuned=not args.no_tuned)
-        extra["gnp100"] = {"k3": bench_single("gnp_n100_p0.08", 3, peak, peak_kind, tuned=False),
-                           "k4": bench_single("gnp_n100_p0.08", 4, peak, peak_kind, tuned=False)}
+        # the 4M-vertex ER graph: the paper's enumeration alone (every root
+        # to the warp-per-task kernel), and with roots of >= 16 higher-rank
+        # neighbours sent to the root-per-CTA kernel
+        extra["er4m"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, base_schedule, tuned=False,
+                                     override={"hub_min_l": 0})
+        extra["er4m_hub16"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, base_schedule, tuned=False,
+                                           override={"hub_min_l": 16})
+        extra["gnp100"] = {"k3": bench_single("gnp_n100_p0.08", 3, peak, peak_kind, base_schedule, tuned=False),
+                           "k4": bench_single("gnp_n100_p0.08", 4, peak, peak_kind, base_schedule, tuned=False)}
     if rank == 0 and world == 1 and not args.no_batch:
+        args.base_schedule = base_schedule
         extra["batch"] = bench_batch(args)
     if rank == 0 and world == 1 and not args.no_serve:
         extra["serve"] = bench_serve(args)

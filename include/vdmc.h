@@ -88,6 +88,10 @@ typedef struct {
     int32_t hub_split_roots;    /* how many of the largest roots are split (>= 0) */
     int32_t hub_warps;          /* root-per-CTA kernel: warps per CTA, 16 or 32
                                    (0 = 16) */
+    int32_t d3_bits;            /* root-per-CTA kernel, k = 4: width of the depth-3
+                                   credit counters; 0 = 32 bits when a per-graph
+                                   bound shows that no vertex can reach 2^32 of
+                                   them in one count, else 64; 64 = always 64 */
 } vdmc_schedule_t;
 
 /*
@@ -237,8 +241,9 @@ vdmc_status vdmc_count_edges(vdmc_graph *g, int k, uint64_t *out_dev, void *stre
 
 /*
  * The rows of vdmc_count_edges: edge i is {u[i], v[i]}, u[i] < v[i] original
- * ids, ascending; flags[i] bit 0 = arc u -> v present, bit 1 = arc v -> u.
- * Host arrays of edges_u entries; any may be NULL.  Synchronous.
+ * ids, ascending; flags[i] bit 0 = arc u -> v present, bit 1 = arc v -> u
+ * (always 3 for a graph built with VDMC_GRAPH_UNDIRECTED).  Host arrays of
+ * edges_u entries; any may be NULL.  Synchronous.
  */
 vdmc_status vdmc_graph_edges(vdmc_graph *g, int32_t *u, int32_t *v, uint8_t *flags);
 

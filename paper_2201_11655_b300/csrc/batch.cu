@@ -153,7 +153,7 @@ void plan_free(Plan *p) {
 bool same_schedule(const vdmc_schedule_t &a, const vdmc_schedule_t &b) {
     return a.a_chunk == b.a_chunk && a.warps_per_block == b.warps_per_block && a.blocks_per_sm == b.blocks_per_sm &&
            a.hub_min_l == b.hub_min_l && a.hub_blocks_per_sm == b.hub_blocks_per_sm && a.hub_split == b.hub_split &&
-           a.hub_split_roots == b.hub_split_roots && a.hub_warps == b.hub_warps;
+           a.hub_split_roots == b.hub_split_roots && a.hub_warps == b.hub_warps && a.d3_bits == b.d3_bits;
 }
 
 vdmc_status build_plan(vdmc_graph *const *gs, int num, int k, uint64_t *const *outs, cudaStream_t s, Plan *p) {

@@ -62,7 +62,51 @@ struct Table {
     // column c, 255 if c is not symmetric
     std::vector<uint16_t> ucanon;
     std::vector<uint8_t> ucol;
+    // column of each class in the counting kernels' rank-space accumulator
+    // (acc_col) and its inverse (acc_class); see accumulator_order
+    std::vector<uint8_t> acc_col, acc_class;
 };
+
+// 12-bit index of the 4-tuple (r, a, b, c) from its six pair flags (Fig. 1
+// bit order; the same packing as the kernels' mask4)
+int index4(int fra, int frb, int frc, int fab, int fac, int fbc) {
+    return ((fra & 1) << 11) | ((frb & 1) << 10) | ((frc & 1) << 9) | ((fra >> 1) << 8) | ((fab & 1) << 7) |
+           ((fac & 1) << 6) | ((frb >> 1) << 5) | ((fab >> 1) << 4) | ((fbc & 1) << 3) | ((frc >> 1) << 2) |
+           ((fac >> 1) << 1) | (fbc >> 1);
+}
+
+// Accumulator column order (k = 4).  The root-per-CTA kernel credits a
+// second-hop vertex c of a member v (colour al, h(v, c) = f) in the classes
+// of r-v-c with a partner be of r, and of r-v-{c, c2}; and a second-hop
+// vertex b with a P-neighbour of type (c1, h1) in the classes of r-x-b-c.
+// Those 25 classes come first, each group's new classes next to each other,
+// so that the few atomics one (v, c) or b adds land in one or two 128-byte
+// lines of the vertex's row; the other classes follow in ascending order.
+// Counts do not depend on the order (the un-relabel pass maps it back).
+std::vector<uint8_t> accumulator_order(int k, const std::vector<uint8_t> &lut, int nclasses) {
+    std::vector<uint8_t> order;
+    std::vector<char> used(nclasses, 0);
+    auto take = [&](int idx) {
+        const int c = lut[idx];
+        if (c < nclasses && !used[c]) {
+            used[c] = 1;
+            order.push_back((uint8_t)c);
+        }
+    };
+    if (k == 4) {
+        for (int al = 1; al <= 3; al++)
+            for (int f = 1; f <= 3; f++) {
+                for (int be = 1; be <= 3; be++) take(index4(al, be, 0, 0, f, 0));
+                for (int f2 = 1; f2 <= 3; f2++) take(index4(al, 0, 0, f, f2, 0));
+            }
+        for (int c1 = 1; c1 <= 3; c1++)
+            for (int h1 = 1; h1 <= 3; h1++)
+                for (int f = 1; f <= 3; f++) take(index4(c1, 0, 0, h1, 0, f));
+    }
+    for (int c = 0; c < nclasses; c++)
+        if (!used[c]) order.push_back((uint8_t)c);
+    return order;
+}
 
 bool symmetric(int k, int idx) {
     for (int i = 0; i < k; i++)
@@ -104,6 +148,9 @@ Table build(int k) {
         auto it = std::lower_bound(T.canon.begin(), T.canon.end(), (uint16_t)name[idx]);
         T.lut[idx] = (uint8_t)(it - T.canon.begin());
     }
+    T.acc_class = accumulator_order(k, T.lut, (int)T.canon.size());
+    T.acc_col.assign(T.canon.size(), 255);
+    for (size_t j = 0; j < T.acc_class.size(); j++) T.acc_col[T.acc_class[j]] = (uint8_t)j;
     T.ucol.assign(T.canon.size(), 255);
     for (size_t c = 0; c < T.canon.size(); c++)
         if (symmetric(k, T.canon[c])) {
@@ -134,6 +181,16 @@ const uint16_t *vdmc_host_canon(int k, int *num_classes) {
     if (!t) return nullptr;
     if (num_classes) *num_classes = (int)t->canon.size();
     return t->canon.data();
+}
+
+const uint8_t *vdmc_host_acc_col(int k) {
+    const Table *t = table(k);
+    return t ? t->acc_col.data() : nullptr;
+}
+
+const uint8_t *vdmc_host_acc_class(int k) {
+    const Table *t = table(k);
+    return t ? t->acc_class.data() : nullptr;
 }
 
 const uint8_t *vdmc_host_ucol(int k, int *num_undirected) {

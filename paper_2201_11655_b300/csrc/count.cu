@@ -41,62 +41,73 @@
 
 namespace {
 
-vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, 16};
+vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, 16, 0};
 std::mutex g_sched_mu;
 
 struct DevLut {
     uint8_t *lut[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    uint8_t *ucol[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint8_t *colmap[5][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
+                             {nullptr, nullptr}};
 };
 DevLut g_lut[64];  // per device
 std::mutex g_lut_mu;
 
+// a device copy of a small host table, made once per device (kept for the
+// life of the process)
+cudaError_t device_table(uint8_t **slot, const std::vector<uint8_t> &host) {
+    if (*slot) return cudaSuccess;
+    uint8_t *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)&p, host.size());
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(p, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return e;
+    }
+    *slot = p;
+    return cudaSuccess;
+}
+
 }  // namespace
 
+// motif index -> accumulator column (the kernels' class ids)
 cudaError_t vdmc_device_lut(int k, const uint8_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (dev < 0 || dev >= 64 || (k != 3 && k != 4)) return cudaErrorInvalidValue;
     std::lock_guard<std::mutex> lk(g_lut_mu);
     if (!g_lut[dev].lut[k]) {
-        size_t bytes = (size_t)1 << (k * (k - 1));
-        uint8_t *p = nullptr;
-        e = cudaMalloc((void **)&p, bytes);
+        const size_t nidx = (size_t)1 << (k * (k - 1));
+        const uint8_t *lut = vdmc_host_lut(k), *acc_col = vdmc_host_acc_col(k);
+        std::vector<uint8_t> h(nidx);
+        for (size_t i = 0; i < nidx; i++) h[i] = lut[i] == 255 ? 255 : acc_col[lut[i]];
+        e = device_table(&g_lut[dev].lut[k], h);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpy(p, vdmc_host_lut(k), bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(p);
-            return e;
-        }
-        g_lut[dev].lut[k] = p;
     }
     *out = g_lut[dev].lut[k];
     return cudaSuccess;
 }
 
-// directed column -> undirected column (255: not symmetric), per device
-cudaError_t vdmc_device_ucol(int k, const uint8_t **out) {
+// accumulator column -> output column: the class itself (directed), or its
+// undirected column (255 where the class is not symmetric)
+cudaError_t vdmc_device_colmap(int k, bool undirected, const uint8_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (dev < 0 || dev >= 64 || (k != 3 && k != 4)) return cudaErrorInvalidValue;
     std::lock_guard<std::mutex> lk(g_lut_mu);
-    if (!g_lut[dev].ucol[k]) {
-        int nu = 0;
-        const uint8_t *h = vdmc_host_ucol(k, &nu);
-        const size_t bytes = (size_t)(k == 3 ? 13 : 199);
-        uint8_t *p = nullptr;
-        e = cudaMalloc((void **)&p, bytes);
+    uint8_t **slot = &g_lut[dev].colmap[k][undirected ? 1 : 0];
+    if (!*slot) {
+        const int C = k == 3 ? 13 : 199;
+        const uint8_t *acc_class = vdmc_host_acc_class(k);
+        const uint8_t *ucol = vdmc_host_ucol(k, nullptr);
+        std::vector<uint8_t> h(C);
+        for (int j = 0; j < C; j++) h[j] = undirected ? ucol[acc_class[j]] : acc_class[j];
+        e = device_table(slot, h);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(p);
-            return e;
-        }
-        g_lut[dev].ucol[k] = p;
     }
-    *out = g_lut[dev].ucol[k];
+    *out = *slot;
     return cudaSuccess;
 }
 
@@ -126,12 +137,21 @@ __global__ void task_fill(const int64_t *rowptr, const int64_t *pbeg, const int6
     for (int32_t j = 0; j < t; j++) tasks[o + j] = Task{r, j, t, 0};
 }
 
+// +n for vertex (rank) v in column cls of its output row
+__device__ __forceinline__ void credit_n(const Csr &g, uint64_t *out, const int32_t *new2old, uint32_t v, int C,
+                                         uint32_t cls, uint32_t n) {
+    if (!in_bounds(g, v < g.n)) return;
+    const int32_t o = row_of(new2old, v);
+    if (!in_bounds(g, o >= 0 && o < g.n)) return;
+    atomicAdd((unsigned long long *)&out[(int64_t)o * C + cls], (unsigned long long)n);
+}
+
 // Per-edge mode (the edge variant of the Discussion): each set credits the
 // edges of G_U inside it instead of its vertices.  Edge ids: the entries of
 // the upper rows in rank order (the edge {u, v}, u < v in rank, is entry
 // v of u's upper row, id ebase[u] + its position there); erow maps an id to
-// its output row.  ucol maps a directed class to its undirected column
-// (undirected graphs) or is null.
+// its output row.  ucol maps the kernel's class id (accumulator column) to
+// the output column (vdmc_device_colmap).
 struct EdgeDesc {
     const int64_t *ebase;
     const int64_t *erow;
@@ -156,7 +176,7 @@ __device__ __forceinline__ int64_t edge_id(const Csr &g, const int64_t *ebase, u
 __device__ __forceinline__ void edge_credit(const Csr &g, const EdgeDesc &E, uint64_t *out, int64_t eid,
                                             uint32_t cls) {
     if (eid < 0) return;
-    const uint32_t c = E.ucol ? (uint32_t)__ldg(E.ucol + cls) : cls;
+    const uint32_t c = (uint32_t)__ldg(E.ucol + cls);
     if (!in_bounds(g, c < (uint32_t)E.cout && eid < g.nnz / 2)) return;
     const int64_t row = __ldg(E.erow + eid);
     atomicAdd((unsigned long long *)&out[row * E.cout + c], 1ull);
@@ -180,12 +200,15 @@ __device__ __forceinline__ void edge_set(const Csr &g, const EdgeDesc &E, uint64
     }
 }
 
-// Neighbour lists staged per warp in shared memory: N+(r) and the parts of
-// N(a) and N(b) above the root (every adjacency test of a set asks about two
-// members of rank > r), when they fit; otherwise the tests search the CSR
-// rows in global memory.
-constexpr int STAGE_P = 64, STAGE_R = 128;
-constexpr int STAGE_WORDS = STAGE_P + 2 * STAGE_R;  // per warp
+// Every adjacency test of a set asks about two members of rank > r, so it
+// searches the part of a member's row above the root.  N+(r), which every
+// candidate is tested against, is staged per warp in shared memory when it
+// fits; so is N(a) above r on the flattened k = 4 walk, where all lanes use
+// it for every b.  The rows of b are searched in global memory (staging each
+// b's row as well measured slower on the power-law workload: they are short
+// and the copies cost more than they save).
+constexpr int STAGE_P = 64, STAGE_A = 128;
+constexpr int STAGE_WORDS = STAGE_P + STAGE_A;  // per warp
 
 struct View {
     const uint32_t *s;  // staged entries (shared memory), or nullptr
@@ -305,7 +328,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             const int64_t a_beg = __ldg(g.rowptr + a), a_end = __ldg(g.rowptr + a + 1);
             if (!in_bounds(g, a_beg >= 0 && a_beg <= a_end && a_end <= G.nnz)) break;
             const int64_t a_up = upper_row(g.col, a_beg, a_end, (uint32_t)r);  // N(a) with rank > r
-            const View VA = stage(g, lists + STAGE_P, a_up, a_end, STAGE_R, lane);
+            const View VA{nullptr, a_up, a_end};
             if (K == 3) {
                 // star: b in P after a
                 for (int32_t ib = ia + 1 + lane; ib < L; ib += 32) {
@@ -325,6 +348,122 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
                     set3(a, b, ia, -1, eb & 3u, cls);
                 }
+            } else if (!EDGE && VP.s != nullptr && a_end - a_up <= STAGE_A) {
+                // Flattened walk of every set with this a, lanes on consecutive
+                // (b, c) work items (short candidate lists would leave most
+                // lanes idle).  b-items: the members of P after a, then the
+                // entries of N(a) above r that are not in P.  Candidates c of a
+                // b in P: the members of P after b (1,1,1), N(a) \ P (1,1,2),
+                // N(b) \ N(a) \ P (1,1,2); of a b at depth 2: N(a) \ P after b
+                // (1,2,2), N(b) \ (N(a) u P) (1,2,3) -- the same sets, shapes and
+                // member order as the nested loops below.  32 b-items at a time,
+                // one per lane; the owner of work item j is found by a binary
+                // search over the lanes' inclusive sums.  Credits to b are
+                // combined over the lanes holding the same (b, class).
+                const View NA = stage(g, lists + STAGE_P, a_up, a_end, STAGE_A, lane);  // N(a) above r
+                const int32_t la = (int32_t)(a_end - a_up);
+                const int32_t n1 = L - 1 - ia;
+                const int32_t nitems = n1 + la;
+                for (int32_t it0 = 0; it0 < nitems; it0 += 32) {
+                    const int32_t it = it0 + lane;
+                    uint32_t b = 0u, frb = 0u, fab = 0u;
+                    int32_t cnt = 0, pos = 0;  // position of b in P, or in N(a) above r
+                    int64_t b_up = 0, b_end = 0;
+                    if (it < nitems) {
+                        const bool inp = it < n1;
+                        pos = inp ? ia + 1 + it : it - n1;
+                        const uint32_t eb = inp ? VP.s[pos] : NA.s[pos];
+                        b = eb >> 2;
+                        bool ok = in_bounds(g, b < G.n);
+                        if (inp) {
+                            frb = eb & 3u;
+                            fab = view_find(g, NA, b);
+                        } else {
+                            fab = eb & 3u;
+                            ok = ok && !view_find(g, VP, b);  // a member of P is not at depth 2
+                        }
+                        if (ok) {
+                            const int64_t bb = __ldg(g.rowptr + b);
+                            b_end = __ldg(g.rowptr + b + 1);
+                            if (in_bounds(g, bb >= 0 && bb <= b_end && b_end <= G.nnz)) {
+                                b_up = upper_row(g.col, bb, b_end, (uint32_t)r);
+                                const int32_t lb = (int32_t)(b_end - b_up);
+                                cnt = inp ? (L - 1 - pos) + la + lb : (la - pos - 1) + lb;
+                            }
+                        }
+                    }
+                    int32_t incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    for (int32_t j0 = 0; j0 < total; j0 += 32) {
+                        const int32_t j = j0 + lane;
+                        int32_t w = 0;
+#pragma unroll
+                        for (int sh = 16; sh >= 1; sh >>= 1)
+                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                        const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
+                        const uint32_t frbo = __shfl_sync(0xffffffffu, frb, w);
+                        const uint32_t fabo = __shfl_sync(0xffffffffu, fab, w);
+                        const int32_t poso = __shfl_sync(0xffffffffu, pos, w);
+                        const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
+                        const int64_t bupo = __shfl_sync(0xffffffffu, b_up, w);
+                        const int64_t bendo = __shfl_sync(0xffffffffu, b_end, w);
+                        const bool inpo = it0 + w < n1;
+                        uint32_t c = 0u, cls = 255u;
+                        if (j < total) {
+                            int32_t off = j - start;
+                            if (inpo) {
+                                const int32_t n111 = L - 1 - poso;
+                                if (off < n111) {  // (1,1,1)
+                                    const uint32_t ec = VP.s[poso + 1 + off];
+                                    c = ec >> 2;
+                                    const uint32_t fac = view_find(g, NA, c);
+                                    const uint32_t fbc = search_row(g.col, bupo, bendo, c);
+                                    cls = lut[mask4(fra, frbo, ec & 3u, fabo, fac, fbc)];
+                                } else if ((off -= n111) < la) {  // (1,1,2), c adjacent to a
+                                    const uint32_t ec = NA.s[off];
+                                    c = ec >> 2;
+                                    if (!view_find(g, VP, c))
+                                        cls = lut[mask4(fra, frbo, 0u, fabo, ec & 3u,
+                                                        search_row(g.col, bupo, bendo, c))];
+                                } else {  // (1,1,2), c adjacent to b only
+                                    const uint32_t ec = __ldg(g.col + bupo + (off - la));
+                                    c = ec >> 2;
+                                    if (!view_find(g, VP, c) && !view_find(g, NA, c))
+                                        cls = lut[mask4(fra, frbo, 0u, fabo, 0u, ec & 3u)];
+                                }
+                            } else {
+                                const int32_t n122 = la - poso - 1;
+                                if (off < n122) {  // (1,2,2)
+                                    const uint32_t ec = NA.s[poso + 1 + off];
+                                    c = ec >> 2;
+                                    if (!view_find(g, VP, c))
+                                        cls = lut[mask4(fra, 0u, 0u, fabo, ec & 3u, search_row(g.col, bupo, bendo, c))];
+                                } else {  // (1,2,3)
+                                    const uint32_t ec = __ldg(g.col + bupo + (off - n122));
+                                    c = ec >> 2;
+                                    if (!view_find(g, VP, c) && !view_find(g, NA, c))
+                                        cls = lut[mask4(fra, 0u, 0u, fabo, 0u, ec & 3u)];
+                                }
+                            }
+                            if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
+                        }
+                        const bool hit = cls != 255u;
+                        if (hit) {
+                            hinc(hist_r, cls);
+                            hinc(hist_a, cls);
+                            credit(g, out, G.new2old, c, C, cls);
+                            nsets++;
+                        }
+                        const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
+                        const uint32_t grp = __match_any_sync(0xffffffffu, key);
+                        if (hit && lane == __ffs(grp) - 1) credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
+                    }
+                }
             } else {
                 // (A1) b in P after a
                 for (int32_t ib = ia + 1; ib < L; ib++) {
@@ -335,7 +474,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
                     if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
                     const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
-                    const View VB = stage(g, lists + STAGE_P + STAGE_R, b_up, b_end, STAGE_R, lane);
+                    const View VB{nullptr, b_up, b_end};
                     // (1,1,1): c in P after b
                     for (int32_t ic = ib + 1 + lane; ic < L; ic += 32) {
                         const uint32_t ec = view_entry(g, VP, pb + ic);
@@ -376,7 +515,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     const int64_t b_beg = __ldg(g.rowptr + b), b_end = __ldg(g.rowptr + b + 1);
                     if (!in_bounds(g, b_beg >= 0 && b_beg <= b_end && b_end <= G.nnz)) break;
                     const int64_t b_up = upper_row(g.col, b_beg, b_end, (uint32_t)r);
-                    const View VB = stage(g, lists + STAGE_P + STAGE_R, b_up, b_end, STAGE_R, lane);
+                    const View VB{nullptr, b_up, b_end};
                     // (1,2,2): c in N(a) after b, c not in N(r)
                     for (int64_t x = xb + 1 + lane; x < a_end; x += 32) {
                         const uint32_t ec = view_entry(g, VA, x);
@@ -406,16 +545,15 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
     }
 }
 
-// out[new2old[r]] = acc[r] (+ the depth-3 credits of r, k = 4), one warp
-// per row (coalesced row copies).  The depth-3 credits are n * VDMC_D3_COLS
-// counters as 32-bit low words d3 followed by as many high words; column d
-// holds the sets r' - x - b - c credited to c whose class is the d-th
-// smallest of the depth-3 path classes (d3_column); unused columns stay zero.
-// With ucol (undirected graphs) directed column c is written to output
-// column ucol[c] of Cout, and skipped when it has none (255).
-__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint32_t *__restrict__ d3,
+// out[new2old[r]] = acc[r] (+ the depth-3 credits d3[r], k = 4), one warp
+// per row (coalesced row copies).  Column d of d3 holds the sets r' - x - b - c
+// credited to c whose class is the d-th smallest of the depth-3 path classes
+// (d3_column); unused columns stay zero.
+// Accumulator column c goes to output column colmap[c] of Cout (its class,
+// or its undirected column), and nowhere when that is 255.
+__global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint64_t *__restrict__ d3, int d3_narrow,
                                const uint8_t *__restrict__ lut, const int32_t *__restrict__ new2old, int32_t n,
-                               int C, const uint8_t *__restrict__ ucol, int Cout, uint64_t *__restrict__ out) {
+                               int C, const uint8_t *__restrict__ colmap, int Cout, uint64_t *__restrict__ out) {
     __shared__ int d3cls[VDMC_D3_COLS];
     if (threadIdx.x < VDMC_D3_COLS) d3cls[threadIdx.x] = -1;
     __syncthreads();
@@ -433,12 +571,12 @@ __global__ void unrelabel_rows(const uint64_t *__restrict__ acc, const uint32_t 
     for (int c = lane; c < C; c += 32) {
         uint64_t v = acc[r * C + c];
         if (d3) {
-            const uint32_t *d3hi = d3 + (int64_t)n * VDMC_D3_COLS;
             for (int j = 0; j < VDMC_D3_COLS; j++)
                 if (d3cls[j] == c)
-                    v += ((uint64_t)__ldg(d3hi + r * VDMC_D3_COLS + j) << 32) | __ldg(d3 + r * VDMC_D3_COLS + j);
+                    v += d3_narrow ? (uint64_t)__ldg(reinterpret_cast<const uint32_t *>(d3) + r * VDMC_D3_COLS + j)
+                                   : __ldg(d3 + r * VDMC_D3_COLS + j);
         }
-        const int oc = ucol ? (int)__ldg(ucol + c) : c;
+        const int oc = (int)__ldg(colmap + c);
         if (oc < Cout) out[(int64_t)o * Cout + oc] = v;
     }
 }
@@ -533,6 +671,36 @@ __global__ void root_cost_kernel(Csr g, int32_t n, int k, int32_t hub_min_l, uns
             cost[r] = acc + (unsigned long long)(pe - rb) + sets;
         }
     }
+}
+
+// Bound on the depth-3 credits of one vertex c in one count: every such set
+// is a path r - x - b - c, so their number is at most
+// B(c) = sum over b in N(c) of sum over x in N(b) of d(x).  When every B(c) is
+// below 2^32 the credits fit 32-bit counters (half the array, so more of it
+// stays in L2).  s1[v] = sum over x in N(v) of d(x); then max over c of B(c).
+__global__ void d3_bound_s1(const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, int32_t n,
+                            unsigned long long *__restrict__ s1) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    unsigned long long acc = 0;
+    for (int64_t e = rowptr[w] + lane; e < rowptr[w + 1]; e += 32) {
+        const uint32_t x = col[e] >> 2;
+        acc += (unsigned long long)(rowptr[x + 1] - rowptr[x]);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) s1[w] = acc;
+}
+
+__global__ void d3_bound_max(const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, int32_t n,
+                             const unsigned long long *__restrict__ s1, unsigned long long *__restrict__ mx) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    unsigned long long acc = 0;
+    for (int64_t e = rowptr[w] + lane; e < rowptr[w + 1]; e += 32) acc += s1[col[e] >> 2];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicMax(mx, acc);
 }
 
 size_t smem_bytes(int k, int warps) {
@@ -634,10 +802,32 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     // depth-3 credits of the root-per-CTA kernel (k = 4): one column per path
     // class (16 per vertex) instead of 199, so that more reductions stay in L2
     uint64_t *d3 = nullptr;
+    bool narrow = false;
     if (k == 4 && g->nhubs > 0 && g->n > 0) {
+        if (g->d3_mode == 0) {
+            // once per graph: can a depth-3 counter reach 2^32 in one count?
+            unsigned long long *s1 = nullptr, *mx = nullptr, hmx = 0;
+            VDMC_CUDA_TRY(vdmc_malloc(&s1, sizeof(unsigned long long) * (size_t)g->n, s));
+            cudaError_t e = vdmc_malloc(&mx, sizeof(unsigned long long), s);
+            const unsigned blocks = (unsigned)(((int64_t)g->n * 32 + 255) / 256);
+            if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) {
+                d3_bound_s1<<<blocks, 256, 0, s>>>(g->rowptr, g->col, g->n, s1);
+                d3_bound_max<<<blocks, 256, 0, s>>>(g->rowptr, g->col, g->n, s1, mx);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hmx, mx, sizeof hmx, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            vdmc_free(s1, s);
+            vdmc_free(mx, s);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VDMC_ERR_OOM : VDMC_ERR_CUDA;
+            g->d3_mode = hmx < (1ull << 32) ? 1 : 2;
+        }
         if (!g->d3acc) VDMC_CUDA_TRY(vdmc_malloc(&g->d3acc, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
         d3 = g->d3acc;
-        VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
+        narrow = g->d3_mode == 1 && sch.d3_bits != 64;
+        const size_t width = narrow ? sizeof(uint32_t) : sizeof(uint64_t);
+        VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, width * (size_t)g->n * VDMC_D3_COLS, s));
     }
     const uint8_t *lut = nullptr;
     VDMC_CUDA_TRY(device_lut(k, &lut));
@@ -647,8 +837,8 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         // with the warp kernel; the caller's stream waits for both
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
         VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vdmc_status st = vdmc_hub_launch(g, k, acc, d3, lut, lo, hi, sch.hub_blocks_per_sm, sch.hub_split,
-                                          sch.hub_split_roots, sch.hub_warps, g->side);
+        vdmc_status st = vdmc_hub_launch(g, k, acc, d3, narrow ? 1 : 0, lut, lo, hi, sch.hub_blocks_per_sm,
+                                          sch.hub_split, sch.hub_split_roots, sch.hub_warps, g->side);
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));
     }
@@ -656,11 +846,11 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
     if (g->nhubs > 0) VDMC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
     if (st != VDMC_OK) return st;
     if (g->n > 0) {
-        const uint8_t *ucol = nullptr;
-        if (g->undirected) VDMC_CUDA_TRY(vdmc_device_ucol(k, &ucol));
+        const uint8_t *colmap = nullptr;
+        VDMC_CUDA_TRY(vdmc_device_colmap(k, g->undirected != 0, &colmap));
         const int Cout = g->undirected ? vdmc_num_classes_undirected(k) : C;
-        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, reinterpret_cast<const uint32_t *>(d3), lut,
-                                                                   g->new2old, g->n, C, ucol, Cout, out);
+        unrelabel_rows<<<(unsigned)((g->n + 7) / 8), 256, 0, s>>>(acc, d3, narrow ? 1 : 0, lut, g->new2old, g->n,
+                                                                   C, colmap, Cout, out);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     // the graph's memory is released behind this point (vdmc_graph_destroy);
@@ -712,13 +902,13 @@ vdmc_status vdmc_count_edges_internal(vdmc_graph *g, int k, uint64_t *out, cudaS
         g->etasks_a_chunk = sch.a_chunk;
     }
     const int Cout = g->undirected ? vdmc_num_classes_undirected(k) : (k == 3 ? 13 : 199);
-    const uint8_t *ucol = nullptr;
-    if (g->undirected) VDMC_CUDA_TRY(vdmc_device_ucol(k, &ucol));
+    const uint8_t *colmap = nullptr;
+    VDMC_CUDA_TRY(vdmc_device_colmap(k, g->undirected != 0, &colmap));
     if (ne > 0) VDMC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t) * (size_t)ne * Cout, s));
     if (g->stats) VDMC_CUDA_TRY(cudaMemsetAsync(g->stats, 0, sizeof(unsigned long long) * VDMC_NSTATS, s));
     GraphDesc d{g->rowptr, g->col, g->pbeg, nullptr, out, g->n, 0, g->nnz};
     st = launch_count(k, d, nullptr, g->etasks, g->netasks, g->qhead, 0, g->n, g->status, g->stats, s, true,
-                      EdgeDesc{g->ebase, g->erow, ucol, Cout});
+                      EdgeDesc{g->ebase, g->erow, colmap, Cout});
     if (st != VDMC_OK) return st;
     VDMC_CUDA_TRY(cudaEventRecord(g->ev_done, s));
     return VDMC_OK;
@@ -813,7 +1003,8 @@ extern "C" vdmc_status vdmc_root_costs(const vdmc_graph *g, int k, uint64_t *cos
 extern "C" vdmc_status vdmc_set_schedule(const vdmc_schedule_t *s) {
     if (!s || s->a_chunk < 1 || s->warps_per_block < 1 || s->warps_per_block > 8 || s->blocks_per_sm < 0 ||
         s->hub_min_l < 0 || s->hub_blocks_per_sm < 1 || s->hub_blocks_per_sm > 8 || s->hub_split < 0 ||
-        s->hub_split > 16 || s->hub_split_roots < 0 || (s->hub_warps != 0 && s->hub_warps != 16 && s->hub_warps != 32))
+        s->hub_split > 16 || s->hub_split_roots < 0 || (s->hub_warps != 0 && s->hub_warps != 16 && s->hub_warps != 32) ||
+        (s->d3_bits != 0 && s->d3_bits != 64))
         return VDMC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched = *s;

@@ -66,10 +66,8 @@ struct HubArgs {
     Csr g;
     const int32_t *new2old;
     uint64_t *out;
-    // k = 4: depth-3 credits (rank space), n * VDMC_D3_COLS counters kept as
-    // 32-bit low words (d3lo) and high words (d3hi, touched only on a carry):
-    // the low words of a 1M-vertex graph (64 MB) stay in L2
-    uint32_t *d3lo, *d3hi;
+    unsigned long long *d3;     // k = 4: n * VDMC_D3_COLS depth-3 credits (rank space)
+    int d3_narrow;              // 1: the credits are 32-bit words (no vertex can reach 2^32 of them)
     unsigned long long *stats;  // [1] sets of hub roots, [2] of those visited one by one (or nullptr)
     const uint8_t *lut_g;
     const int32_t *hubs;
@@ -1168,10 +1166,14 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
 #pragma unroll
                             for (int k = 0; k < 9; k++)
                                 if ((nzo >> k) & 1u) {
+                                    // a reduction: its result is not needed, so the warp
+                                    // does not wait for it (a 32-bit add with a carry
+                                    // check would make it wait on every entry)
                                     const int64_t di = (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1];
-                                    const uint32_t v = sq[w * 9 + k];
-                                    const uint32_t old = atomicAdd(A.d3lo + di, v);
-                                    if ((uint32_t)(old + v) < old) atomicAdd(A.d3hi + di, 1u);  // carry
+                                    if (A.d3_narrow)
+                                        atomicAdd(reinterpret_cast<unsigned int *>(A.d3) + di, sq[w * 9 + k]);
+                                    else
+                                        atomicAdd(A.d3 + di, (unsigned long long)sq[w * 9 + k]);
                                 }
                         }
                         cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
@@ -1392,7 +1394,8 @@ cudaError_t launch_hub(int slots, size_t dsmem, const HubArgs &A, cudaStream_t s
     return cudaGetLastError();
 }
 
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, const uint8_t *lut,
+                            int32_t lo,
                             int32_t hi, int blocks_per_sm, int split, int split_roots, int warps, cudaStream_t s) {
     warps = warps == 32 ? 32 : 16;
     if (g->nhubs <= 0) return VDMC_OK;
@@ -1439,8 +1442,8 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, c
     A.g = Csr{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
     A.new2old = nullptr;  // credits in rank space (see vdmc_count_internal)
     A.out = out;
-    A.d3lo = reinterpret_cast<uint32_t *>(d3);
-    A.d3hi = d3 ? reinterpret_cast<uint32_t *>(d3) + (size_t)g->n * VDMC_D3_COLS : nullptr;
+    A.d3 = (unsigned long long *)d3;
+    A.d3_narrow = d3_narrow;
     A.stats = g->stats;
     A.lut_g = lut;
     A.hubs = g->hubs;

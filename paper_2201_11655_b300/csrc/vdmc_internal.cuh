@@ -65,8 +65,8 @@ struct vdmc_graph {
     int32_t num_graphs;          // > 1 for a graph built by vdmc_graph_create_batch
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
     uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
-    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel: n * VDMC_D3_COLS
-                                 // low 32-bit words, then as many high words (rank space)
+    uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * VDMC_D3_COLS (rank space)
+    int d3_mode;                 // 0 unknown, 1: 32-bit depth-3 credits suffice (d3_bound), 2: 64-bit
     unsigned long long *stats;   // VDMC_NSTATS counters of the last count (vdmc_count_stats)
     int undirected;              // VDMC_GRAPH_UNDIRECTED: every edge carries flags 3, output in undirected classes
     // per-edge counts (vdmc_count_edges), built on first use
@@ -138,11 +138,19 @@ const uint16_t *vdmc_host_canon(int k, int *num_classes);
 // undirected variant: column of each directed class among the symmetric ones
 // (255 = not symmetric), and their number (2 for k = 3, 6 for k = 4)
 const uint8_t *vdmc_host_ucol(int k, int *num_undirected);
+// column of each class in the counting kernels' accumulator, and the class of
+// each accumulator column (classes.cpp: accumulator_order)
+const uint8_t *vdmc_host_acc_col(int k);
+const uint8_t *vdmc_host_acc_class(int k);
 
 // ---- counting (count.cu) ----
 vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, uint64_t *out, cudaStream_t s);
+// device copies (per device, built once): lut maps a motif index to its
+// ACCUMULATOR column (255 = not weakly connected); colmap maps an
+// accumulator column to an output column (directed classes, or undirected
+// columns with 255 where a class is not symmetric)
 cudaError_t vdmc_device_lut(int k, const uint8_t **out);
-cudaError_t vdmc_device_ucol(int k, const uint8_t **out);
+cudaError_t vdmc_device_colmap(int k, bool undirected, const uint8_t **out);
 
 // ---- per-edge counts (edges.cu) ----
 // builds g->ebase, g->erow, g->ekeys, g->eflags on first use (on stream s)
@@ -164,7 +172,7 @@ void vdmc_current_schedule(vdmc_schedule_t *s);
 
 // ---- root-per-CTA kernel (hub.cu) ----
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, const uint8_t *lut, int32_t lo,
-                            int32_t hi, int blocks_per_sm, int split, int split_roots, int warps,
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, const uint8_t *lut,
+                            int32_t lo, int32_t hi, int blocks_per_sm, int split, int split_roots, int warps,
                             cudaStream_t s);
 void vdmc_hub_free(vdmc_graph *g, cudaStream_t s);

@@ -222,8 +222,10 @@ WORKLOADS = {
         100_000, 10.0 / 1.2, 2.3, seed, reciprocity=0.2, max_degree=6_000),
     "chunglu_n300k_m3M_a2.3_r0.2": lambda seed=2: chung_lu(
         300_000, 10.0 / 1.2, 2.3, seed, reciprocity=0.2, max_degree=11_000),
-    # Directed uniform-endpoint ER, 4M vertices, 32M arcs.
+    # Directed uniform-endpoint ER, 4M vertices, 32M arcs, and the same
+    # shape at 1/4 scale (profiling captures).
     "er_n4M_m32M": lambda seed=3: er_uniform(4_000_000, 32_000_000, seed),
+    "er_n1M_m8M": lambda seed=3: er_uniform(1_000_000, 8_000_000, seed),
 }
 
 

@@ -45,7 +45,7 @@ class Schedule(ctypes.Structure):
     _fields_ = [("a_chunk", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("hub_min_l", ctypes.c_int32),
                 ("hub_blocks_per_sm", ctypes.c_int32), ("hub_split", ctypes.c_int32),
-                ("hub_split_roots", ctypes.c_int32), ("hub_warps", ctypes.c_int32)]
+                ("hub_split_roots", ctypes.c_int32), ("hub_warps", ctypes.c_int32), ("d3_bits", ctypes.c_int32)]
 
 
 class WorkModel(ctypes.Structure):
@@ -66,7 +66,7 @@ class CountStats(ctypes.Structure):
 
 
 SCHEDULE_KEYS = ("a_chunk", "warps_per_block", "blocks_per_sm", "hub_min_l", "hub_blocks_per_sm", "hub_split",
-                 "hub_split_roots", "hub_warps")
+                 "hub_split_roots", "hub_warps", "d3_bits")
 
 
 _LIB = None

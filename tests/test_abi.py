@@ -81,11 +81,12 @@ def test_schedule_roundtrip(lib):
     old = vdmc.get_schedule()
     try:
         vdmc.set_schedule(a_chunk=3, warps_per_block=4, blocks_per_sm=2, hub_min_l=7, hub_blocks_per_sm=2,
-                          hub_split=4, hub_split_roots=9, hub_warps=32)
+                          hub_split=4, hub_split_roots=9, hub_warps=32, d3_bits=64)
         assert vdmc.get_schedule() == {"a_chunk": 3, "warps_per_block": 4, "blocks_per_sm": 2,
                                        "hub_min_l": 7, "hub_blocks_per_sm": 2, "hub_split": 4, "hub_split_roots": 9,
-                                       "hub_warps": 32}
-        for bad in ({"hub_split": -1}, {"hub_split": 17}, {"hub_split_roots": -1}, {"hub_warps": 8}):
+                                       "hub_warps": 32, "d3_bits": 64}
+        for bad in ({"hub_split": -1}, {"hub_split": 17}, {"hub_split_roots": -1}, {"hub_warps": 8},
+                    {"d3_bits": 32}):
             with pytest.raises(vdmc.VdmcError):
                 vdmc.set_schedule(**bad)
     finally:

@@ -12,7 +12,8 @@ from paper_2201_11655_b300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [dict(hub_min_l=0), dict(hub_min_l=1), dict(hub_min_l=4, hub_split=3, hub_split_roots=6, hub_warps=32)]
+SCHEDULES = [dict(hub_min_l=0), dict(hub_min_l=1), dict(hub_min_l=4, hub_split=3, hub_split_roots=6, hub_warps=32),
+             dict(hub_min_l=2, d3_bits=64)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -61,7 +62,9 @@ def test_per_edge_counts_vs_oracle(undirected):
             np.testing.assert_array_equal(v, ov)
             arcs = set(zip(s.tolist(), d.tolist()))
             for i in range(len(u)):
-                assert int(f[i]) == ((u[i], v[i]) in arcs) + 2 * ((v[i], u[i]) in arcs)
+                # an undirected graph takes every edge as arcs both ways
+                want_f = 3 if undirected else ((u[i], v[i]) in arcs) + 2 * ((v[i], u[i]) in arcs)
+                assert int(f[i]) == want_f
             for k in (3, 4):
                 got = to_numpy_u64(vdmc.count_edges(g, k))
                 torch.cuda.synchronize()
