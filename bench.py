@@ -500,10 +500,14 @@ def run_ours(args):
         # the 4M-vertex ER graph: the paper's enumeration alone (every root
         # to the warp-per-task kernel), and with roots of >= 16 higher-rank
         # neighbours sent to the root-per-CTA kernel
-        extra["er4m"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, base_schedule, tuned=False,
+        extra["er4m"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, base_schedule, tuned=not args.no_tuned,
                                      override={"hub_min_l": 0})
         extra["er4m_hub16"] = bench_single("er_n4M_m32M", 4, peak, peak_kind, base_schedule, tuned=False,
                                            override={"hub_min_l": 16})
+        # the same power-law graph at the other k
+        other = 3 if k == 4 else 4
+        extra["%s_k%d" % (args.workload, other)] = bench_single(args.workload, other, peak, peak_kind, base_schedule,
+                                                               tuned=not args.no_tuned)
         extra["gnp100"] = {"k3": bench_single("gnp_n100_p0.08", 3, peak, peak_kind, base_schedule, tuned=False),
                            "k4": bench_single("gnp_n100_p0.08", 4, peak, peak_kind, base_schedule, tuned=False)}
     if rank == 0 and world == 1 and not args.no_batch:

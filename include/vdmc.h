@@ -27,6 +27,10 @@
  *     vdmc_get_device_status() after synchronising the stream.
  *   - The library never calls exit(), never traps on the device and never
  *     spins on a device flag.
+ *   - A graph's device memory comes from the device's default stream-ordered
+ *     memory pool (cudaMallocAsync); on the first graph built on a device
+ *     the library lets that pool keep up to 16 GiB of freed memory for reuse
+ *     (its release threshold), so repeated builds do not map memory afresh.
  *   - All counts are exact uint64; no floating point is used anywhere.
  */
 #ifndef VDMC_H
@@ -203,13 +207,17 @@ vdmc_status vdmc_class_lut(int k, uint8_t *lut_out);
  * Per-vertex counts (the VDMC algorithm of "The Algorithm"; proper k-BFS of
  * Lemma 1; BFS structures of Lemma 2; ordering rules of Lemma 3; the
  * direct-adjacency test of the comment after Lemma 4).
- *   g        graph from vdmc_graph_create
+ *   g        graph from vdmc_graph_create (or _ex / _batch)
  *   k        3 or 4
- *   out_dev  device uint64[n * C_k], row-major by ORIGINAL vertex id;
- *            overwritten (not accumulated).  Caller owns it.
+ *   out_dev  device uint64[n * C], C = vdmc_graph_num_classes(g, k) (C_k, or
+ *            the undirected columns for a VDMC_GRAPH_UNDIRECTED graph),
+ *            row-major by ORIGINAL vertex id; overwritten (not accumulated).
+ *            Caller owns it.
  *   stream   cudaStream_t
- * Asynchronous.  Calls on one graph must not overlap (they share the graph's
- * work-queue cursor); use one graph per concurrent stream.
+ * Asynchronous (the first k = 4 count of a graph with hub roots synchronises
+ * `stream` once, to size its depth-3 counters).  Calls on one graph must not
+ * overlap (they share the graph's work-queue cursor); a call waits, on the
+ * device, for the graph's previous call on any stream.
  */
 vdmc_status vdmc_count(vdmc_graph *g, int k, uint64_t *out_dev, void *stream);
 

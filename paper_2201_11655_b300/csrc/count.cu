@@ -321,6 +321,77 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             nsets++;
         };
 
+        if (K == 3 && !EDGE && VP.s != nullptr) {
+            // k = 3 flattened over the task's depth-1 vertices a: a-items (32
+            // at a time, one per lane), each with the candidates b in P after
+            // a (star) and b in N(a) above r, not in P (path); lanes take
+            // consecutive (a, b) items.  Credits to a are combined over the
+            // lanes holding the same (a, class).
+            const int32_t na = task.j < L ? (L - 1 - task.j) / task.stride + 1 : 0;
+            for (int32_t it0 = 0; it0 < na; it0 += 32) {
+                const int32_t it = it0 + lane;
+                uint32_t a = 0u, fra = 0u;
+                int32_t ia = 0, cnt = 0;
+                int64_t a_up = 0, a_end = 0;
+                if (it < na) {
+                    ia = task.j + it * task.stride;
+                    const uint32_t ea = VP.s[ia];
+                    a = ea >> 2;
+                    fra = ea & 3u;
+                    if (in_bounds(g, a < G.n)) {
+                        const int64_t ab = __ldg(g.rowptr + a);
+                        a_end = __ldg(g.rowptr + a + 1);
+                        if (in_bounds(g, ab >= 0 && ab <= a_end && a_end <= G.nnz)) {
+                            a_up = upper_row(g.col, ab, a_end, (uint32_t)r);
+                            cnt = (L - 1 - ia) + (int32_t)(a_end - a_up);
+                        }
+                    }
+                }
+                int32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                for (int32_t j0 = 0; j0 < total; j0 += 32) {
+                    const int32_t j = j0 + lane;
+                    int32_t w = 0;
+#pragma unroll
+                    for (int sh = 16; sh >= 1; sh >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                    const uint32_t ao = __shfl_sync(0xffffffffu, a, w);
+                    const uint32_t frao = __shfl_sync(0xffffffffu, fra, w);
+                    const int32_t iao = __shfl_sync(0xffffffffu, ia, w);
+                    const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
+                    const int64_t aupo = __shfl_sync(0xffffffffu, a_up, w);
+                    const int64_t aendo = __shfl_sync(0xffffffffu, a_end, w);
+                    uint32_t b = 0u, cls = 255u;
+                    if (j < total) {
+                        const int32_t off = j - start, nstar = L - 1 - iao;
+                        if (off < nstar) {  // star: b in P after a
+                            const uint32_t eb = VP.s[iao + 1 + off];
+                            b = eb >> 2;
+                            cls = lut[mask3(frao, eb & 3u, search_row(g.col, aupo, aendo, b))];
+                        } else {  // path: b in N(a) \ N(r)
+                            const uint32_t eb = __ldg(g.col + aupo + (off - nstar));
+                            b = eb >> 2;
+                            if (!view_find(g, VP, b)) cls = lut[mask3(frao, 0u, eb & 3u)];
+                        }
+                        if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
+                    }
+                    const bool hit = cls != 255u;
+                    if (hit) {
+                        hinc(hist_r, cls);
+                        credit(g, out, G.new2old, b, C, cls);
+                        nsets++;
+                    }
+                    const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
+                    const uint32_t grp = __match_any_sync(0xffffffffu, key);
+                    if (hit && lane == __ffs(grp) - 1) credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
+                }
+            }
+        } else
         for (int32_t ia = task.j; ia < L; ia += task.stride) {
             const uint32_t ea = view_entry(g, VP, pb + ia);
             const uint32_t a = ea >> 2, fra = ea & 3u;

@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "vdmc_internal.cuh"
@@ -236,6 +237,25 @@ void free_graph_buffers(vdmc_graph *g) {
     if (g->ev_done) cudaEventDestroy(g->ev_done);
 }
 
+// Graph memory comes from the device's default stream-ordered pool.  By
+// default the pool returns freed memory to the driver at every
+// synchronisation, so each new graph would map its gigabytes afresh; the
+// library lets the pool keep up to VDMC_POOL_KEEP_BYTES of freed memory for
+// reuse (set once per device, on the first graph built there).
+constexpr uint64_t VDMC_POOL_KEEP_BYTES = 16ull << 30;
+std::once_flag g_pool_once[64];
+
+void keep_pool_memory(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(g_pool_once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t keep = VDMC_POOL_KEEP_BYTES, cur = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < keep)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    });
+}
+
 vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int on_device,
                         cudaStream_t s, vdmc_graph *g, const int64_t *goff, int32_t ngroups, uint32_t options) {
     g->n = n;
@@ -243,6 +263,7 @@ vdmc_status create_impl(int32_t n, int64_t m, const int32_t *src, const int32_t 
     g->info.n = n;
     g->info.arcs_in = m;
     VDMC_CUDA_TRY(cudaGetDevice(&g->device));
+    keep_pool_memory(g->device);
     VDMC_CUDA_TRY(vdmc_malloc(&g->qhead, sizeof(unsigned long long), s));
     VDMC_CUDA_TRY(vdmc_malloc(&g->status, sizeof(int), s));
     VDMC_CUDA_TRY(vdmc_malloc(&g->stats, sizeof(unsigned long long) * VDMC_NSTATS, s));

@@ -246,9 +246,16 @@ class Server:
 
 
 class GpuBackend:
-    """Runs jobs with the CUDA library: one torch stream per in-flight job."""
+    """Runs jobs with the CUDA library: one torch stream per in-flight job.
 
-    def __init__(self, device: int = 0):
+    With workers > 0 a job's graph build and count launch run on a pool of
+    host threads (the library's calls release the interpreter lock), so the
+    loop keeps admitting and completing requests while graphs are built; the
+    build of one graph synchronises only its own stream."""
+
+    def __init__(self, device: int = 0, workers: int = 4):
+        import concurrent.futures
+        import threading
         import torch
         from . import vdmc
         self.torch = torch
@@ -256,38 +263,82 @@ class GpuBackend:
         self.device = device
         vdmc.load()
         self.free_streams = []
+        self._lock = threading.Lock()
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=workers) if workers > 0 else None
 
     def _stream(self):
-        return self.free_streams.pop() if self.free_streams else self.torch.cuda.Stream(device=self.device)
+        with self._lock:
+            if self.free_streams:
+                return self.free_streams.pop()
+        return self.torch.cuda.Stream(device=self.device)
+
+    def _run(self, reqs, stream):
+        torch, vdmc = self.torch, self.vdmc
+        torch.cuda.set_device(self.device)
+        k = reqs[0].k
+        g = None
+        try:
+            with torch.cuda.stream(stream):
+                if len(reqs) == 1:
+                    r = reqs[0]
+                    g = vdmc.graph_create(r.n, r.src, r.dst, stream=stream)
+                    offsets = [0, r.n]
+                else:
+                    g = vdmc.graph_create_batch([(r.n, r.src, r.dst) for r in reqs], stream=stream)
+                    offsets = g.offsets
+                out = torch.empty((g.n, vdmc.num_classes(k)), dtype=torch.uint64, device="cuda")
+                vdmc.count(g, k, out=out, stream=stream)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+        except Exception:
+            if g is not None:
+                g.close()
+            raise
+        return {"g": g, "out": out, "ev": ev, "offsets": offsets}
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown(wait=True)
 
     def launch(self, reqs):
-        torch, vdmc = self.torch, self.vdmc
-        k = reqs[0].k
         stream = self._stream()
-        with torch.cuda.stream(stream):
-            if len(reqs) == 1:
-                r = reqs[0]
-                g = vdmc.graph_create(r.n, r.src, r.dst, stream=stream)
-                offsets = [0, r.n]
-            else:
-                g = vdmc.graph_create_batch([(r.n, r.src, r.dst) for r in reqs], stream=stream)
-                offsets = g.offsets
-            out = torch.empty((g.n, vdmc.num_classes(k)), dtype=torch.uint64, device="cuda")
-            vdmc.count(g, k, out=out, stream=stream)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        return {"g": g, "out": out, "ev": ev, "stream": stream, "offsets": offsets, "n": len(reqs)}
+        h = {"stream": stream, "n": len(reqs)}
+        if self.pool is None:
+            try:
+                h.update(self._run(reqs, stream))
+            except Exception:
+                self._release(stream)
+                raise
+        else:
+            h["future"] = self.pool.submit(self._run, reqs, stream)
+        return h
+
+    def _release(self, stream):
+        with self._lock:
+            self.free_streams.append(stream)
 
     def done(self, h) -> bool:
+        fut = h.get("future")
+        if fut is not None:
+            if not fut.done():
+                return False
+            if fut.exception() is not None:
+                return True  # finish() raises it
+            h.update(fut.result())
+            h["future"] = None
         return h["ev"].query()
 
     def finish(self, h):
+        fut = h.get("future")
+        if fut is not None:  # the build or launch failed in its worker
+            self._release(h["stream"])
+            fut.result()
         g = h["g"]
         try:
             st = g.device_status()
         finally:
             g.close()  # stream-ordered release: waits for no other job
-            self.free_streams.append(h["stream"])
+            self._release(h["stream"])
         if st != 0:
             raise RuntimeError("device status %d" % st)
         off = h["offsets"]
@@ -354,13 +405,15 @@ def sweep(num: int = 2000, n_hi: int = 50_000, loads="0.25,0.5,0.75,0.9", seed: 
         else:
             arr = np.cumsum(rng.exponential(1.0 / (rho * cap), num))
         reqs = [Request(rid=r.rid, n=r.n, src=r.src, dst=r.dst, k=r.k, arrival=float(a)) for r, a in zip(base, arr)]
-        srv = Server(GpuBackend(), memory_budget=budget, max_inflight=6, small_n=20_000, batch_max=64,
+        backend = GpuBackend()
+        srv = Server(backend, memory_budget=budget, max_inflight=6, small_n=20_000, batch_max=64,
                      batch_wait=0.002)
         t1 = time.perf_counter()
         srv.submit_stream(reqs)
         done = srv.run()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t1
+        backend.close()
         points.append({"offered_load": rho if rho is not None else "burst",
                        "arrival_rate_hz": (rho * cap) if rho is not None else None,
                        "requests_per_s": len(done) / wall, "wall_s": wall,

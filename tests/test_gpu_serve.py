@@ -25,7 +25,8 @@ def _cuda():
     vdmc.load()
 
 
-def test_served_equals_alone():
+@pytest.mark.parametrize("workers", [4, 0])
+def test_served_equals_alone(workers):
     from paper_2201_11655_b300.serve import GpuBackend, Request, Server
     rng = np.random.default_rng(3)
     reqs = []
@@ -38,7 +39,8 @@ def test_served_equals_alone():
         else:
             n, s, d = synth.chung_lu(int(rng.integers(30, 300)), float(rng.uniform(1.5, 5)), 2.5, 1000 + i)
         reqs.append(Request(rid=i, n=n, src=s, dst=d, k=3 + (i % 3 == 0), arrival=i * 2e-4))
-    srv = Server(GpuBackend(), memory_budget=8 << 30, max_inflight=4, small_n=2000, batch_max=16, batch_wait=1e-3)
+    backend = GpuBackend(workers=workers)
+    srv = Server(backend, memory_budget=8 << 30, max_inflight=4, small_n=2000, batch_max=16, batch_wait=1e-3)
     srv.submit_stream(reqs)
     done = srv.run()
     torch.cuda.synchronize()
@@ -53,3 +55,4 @@ def test_served_equals_alone():
             np.testing.assert_array_equal(got, want)
     st = Server.latency_stats(done)
     assert st["count"] == len(reqs) and st["p99_ms"] >= st["p50_ms"]
+    backend.close()
