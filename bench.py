@@ -185,6 +185,17 @@ def oracle_sample(n, s, d, k, target_s, threads=None):
                       "subtracted)" % (threads, lo, hi, found, k, el, build_s), "lo": lo, "hi": hi}
 
 
+_WORKLOADS = {}
+
+
+def workload(name):
+    """synth.workload(name), drawn once per process (the sub-benchmarks reuse graphs)."""
+    from paper_2201_11655_b300 import synth
+    if name not in _WORKLOADS:
+        _WORKLOADS[name] = synth.workload(name)
+    return _WORKLOADS[name]
+
+
 def timed_ms(fn, reps=3, stream=None):
     """Best of `reps` device times (CUDA events on the launching stream) after one untimed call."""
     import torch
@@ -239,7 +250,7 @@ def bench_single(name, k, peak, peak_kind, base_schedule, tuned=True, override=N
     size bucket if any, then `override`."""
     import torch
     from paper_2201_11655_b300 import autotune, synth, vdmc
-    n, s, d = synth.workload(name)
+    n, s, d = workload(name)
     saved = vdmc.get_schedule()
     vdmc.set_schedule(**base_schedule)
     sched = autotune.apply_tuned(k, n, len(s)) if tuned else None
@@ -266,6 +277,49 @@ def bench_single(name, k, peak, peak_kind, base_schedule, tuned=True, override=N
                "schedule_source": ("tuned" if sched else "default") + ("+%s" % override if override else ""),
                "roofline": roofline_of(model, ms, peak, peak_kind, "vdmc_count (all kernels of one count)")}
         res.update(rates(stats, ms))
+        return res
+    finally:
+        g.close()
+        vdmc.set_schedule(**saved)
+
+
+def bench_variant(name, k, peak, peak_kind, base_schedule, undirected=False, per_edge=False, tuned=True, reps=3):
+    """The undirected variant and the per-edge counts on a named workload:
+    device time per count, sets/s (from the count's set counters), byte
+    roofline (per-edge: the output is one row per edge of G_U)."""
+    import torch
+    from paper_2201_11655_b300 import autotune, synth, vdmc
+    n, s, d = workload(name)
+    saved = vdmc.get_schedule()
+    vdmc.set_schedule(**base_schedule)
+    sched = autotune.apply_tuned(k, n, len(s)) if tuned else None
+    g = vdmc.graph_create(n, torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), undirected=undirected)
+    try:
+        C = g.num_classes(k)
+        ne = g.info()["edges_u"]
+        out = torch.empty((ne if per_edge else n, C), dtype=torch.uint64, device="cuda")
+        fn = (lambda: vdmc.count_edges(g, k, out)) if per_edge else (lambda: vdmc.count(g, k, out))
+        ms = timed_ms(fn, reps=reps)
+        torch.cuda.synchronize()
+        if g.device_status() != 0:
+            raise RuntimeError("device status error in %s" % name)
+        st = g.count_stats()
+        inst = st["sets_enumerated"] + st["sets_by_signature"]
+        if not per_edge and int(out.view(torch.int64).sum().item()) != k * inst:
+            raise RuntimeError("set counters disagree with the counts")
+        model = g.work_model(k)
+        if per_edge:  # the output is one row per edge instead of per vertex
+            model = dict(model)
+            out_b = 8 * ne * C + 4 * n
+            for key in ("bytes", "bytes_per_use"):
+                model[key] = model[key] - model["output_bytes"] + out_b
+            model["output_bytes"] = out_b
+        res = {"workload": name, "k": k, "undirected": undirected, "per_edge": per_edge, "n": n,
+               "edges_u": ne, "columns": C, "ms_per_count": ms, "instances": inst,
+               "instances_per_s": inst / (ms / 1e3), "schedule": vdmc.get_schedule(),
+               "schedule_source": "tuned" if sched else "default",
+               "roofline": roofline_of(model, ms, peak, peak_kind, "vdmc_count_edges" if per_edge else "vdmc_count")}
+        res.update(rates(st, ms))
         return res
     finally:
         g.close()
@@ -388,7 +442,7 @@ def run_ours(args):
     base_schedule = vdmc.get_schedule()  # the library default, before any tuned entry
     k = args.k
     C = vdmc.num_classes(k)
-    n, s, d = synth.workload(args.workload)
+    n, s, d = workload(args.workload)
     m = int(s.size)
     tuned = None
     if not args.no_tuned:
@@ -508,6 +562,13 @@ def run_ours(args):
         other = 3 if k == 4 else 4
         extra["%s_k%d" % (args.workload, other)] = bench_single(args.workload, other, peak, peak_kind, base_schedule,
                                                                tuned=not args.no_tuned)
+        # the variants of the Discussion / Tables 1-2: undirected motifs of the
+        # same power-law graph, per-edge counts of the 1M ER graph (the per-edge
+        # path enumerates every set, so not the hub-heavy graph)
+        extra["undirected"] = bench_variant(args.workload, k, peak, peak_kind, base_schedule, undirected=True,
+                                            tuned=not args.no_tuned)
+        extra["per_edge"] = bench_variant("er_n1M_m8M", 4, peak, peak_kind, base_schedule, per_edge=True,
+                                          tuned=False)
         extra["gnp100"] = {"k3": bench_single("gnp_n100_p0.08", 3, peak, peak_kind, base_schedule, tuned=False),
                            "k4": bench_single("gnp_n100_p0.08", 4, peak, peak_kind, base_schedule, tuned=False)}
     if rank == 0 and world == 1 and not args.no_batch:

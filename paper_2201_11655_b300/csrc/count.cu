@@ -795,7 +795,9 @@ vdmc_status launch_count(int k, const GraphDesc &single, const GraphDesc *multi,
     VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     auto kern = edge ? ((k == 3) ? count_kernel<3, true> : count_kernel<4, true>)
                      : ((k == 3) ? count_kernel<3, false> : count_kernel<4, false>);
-    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // per-kernel attribute: the largest size any schedule uses, so that host
+    // threads with different schedules never lower it under each other
+    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(k, 8)));
     int per_sm = 0;
     VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1017,7 +1019,10 @@ extern "C" vdmc_status vdmc_work_model(const vdmc_graph *g, int k, vdmc_work_mod
         cudaError_t e = cudaMemset(d, 0, sizeof h);
         if (e == cudaSuccess && !in_smem) e = cudaMalloc((void **)&gbits, sizeof(uint32_t) * (size_t)words * grid);
         const size_t dsm = in_smem ? sizeof(uint32_t) * (size_t)words : 0;
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(work_model_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        // per-kernel attribute: set to the largest bitmap, never lowered (see launch_hub)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(work_model_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(46000 * sizeof(uint32_t)));
         if (e == cudaSuccess) {
             Csr c{g->rowptr, g->col, g->pbeg, g->n, g->nnz, g->status};
             work_model_kernel<<<grid, 256, dsm>>>(c, g->n, k, gbits, words, in_smem ? 1 : 0, d);
@@ -1205,7 +1210,7 @@ extern "C" vdmc_status vdmc_count_csr_noalloc(int32_t n, int64_t nnz, const int6
     int sms = 0, per_sm = 0;
     VDMC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     auto kern = (k == 3) ? count_kernel<3, false> : count_kernel<4, false>;
-    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VDMC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(k, 8)));
     VDMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
     const int64_t grid = (int64_t)sms * std::max(1, per_sm);
     GraphDesc d{rowptr, col, pbeg, new2old, out_dev, n, 0, nnz};

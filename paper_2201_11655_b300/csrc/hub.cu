@@ -1388,7 +1388,12 @@ int vdmc_hub_count(const vdmc_graph *g) { return g->nhubs; }
 
 template <int K, int W>
 cudaError_t launch_hub(int slots, size_t dsmem, const HubArgs &A, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(hub_kernel<K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+    // The attribute is per kernel, not per launch: host threads launching for
+    // graphs of different sizes must not lower it under each other, so it is
+    // always set to the largest P bitmap this CTA size may use.
+    const int dmax = (int)(hub_smem_bits_max_words(W) * 4);
+    if ((int)dsmem > dmax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(hub_kernel<K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax);
     if (e != cudaSuccess) return e;
     hub_kernel<K, W><<<(unsigned)slots, W * 32, dsmem, s>>>(A);
     return cudaGetLastError();

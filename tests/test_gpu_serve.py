@@ -56,3 +56,36 @@ def test_served_equals_alone(workers):
     st = Server.latency_stats(done)
     assert st["count"] == len(reqs) and st["p99_ms"] >= st["p50_ms"]
     backend.close()
+
+
+def test_threads_counting_different_graphs_concurrently():
+    # host threads build and count graphs of different sizes at the same time
+    # (as the serving backend's workers do); each result equals the graph
+    # counted alone
+    import concurrent.futures
+    from paper_2201_11655_b300 import vdmc
+    old = vdmc.get_schedule()
+    vdmc.set_schedule(hub_min_l=8)
+    try:
+        graphs = [synth.chung_lu(int(n), 4.0, 2.2, 50 + i, reciprocity=0.2)
+                  for i, n in enumerate((300, 3000, 20000, 800, 60000, 1500, 9000, 40000))]
+        alone = [gpu_count(n, s, d, 4) for n, s, d in graphs]
+
+        def work(i):
+            torch.cuda.set_device(0)
+            n, s, d = graphs[i]
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                with vdmc.graph_create(n, s, d, stream=stream) as g:
+                    out = vdmc.count(g, 4, stream=stream)
+                    stream.synchronize()
+                    assert g.device_status() == 0
+                    return to_numpy_u64(out)
+
+        for rep in range(3):
+            with concurrent.futures.ThreadPoolExecutor(max_workers=4) as ex:
+                got = list(ex.map(work, range(len(graphs))))
+            for i in range(len(graphs)):
+                np.testing.assert_array_equal(got[i], alone[i], err_msg="graph %d rep %d" % (i, rep))
+    finally:
+        vdmc.set_schedule(**old)
