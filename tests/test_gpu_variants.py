@@ -101,3 +101,34 @@ def test_per_edge_totals_identity_midsize():
                             p += 1
                 e_m = int(((adj + adj.T) > 0).sum()) // 2
                 assert y[c] * k == e_m * x[c], (k, c)
+
+
+def test_variants_relabel_and_direction_invariants_midsize():
+    # properties that hold at any size: an undirected count does not depend on
+    # arc directions (reversing all arcs, or adding every reverse arc, leaves
+    # it unchanged); relabelling the vertices permutes rows (vertex counts)
+    # and edge rows (per-edge counts, matched through vdmc_graph_edges)
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = synth.chung_lu(20000, 5.0, 2.3, 11, reciprocity=0.2)
+    vdmc.set_schedule(hub_min_l=16)
+    with vdmc.graph_create(n, s, d, undirected=True) as g:
+        base = to_numpy_u64(vdmc.count(g, 4))
+    with vdmc.graph_create(n, d, s, undirected=True) as g:
+        np.testing.assert_array_equal(to_numpy_u64(vdmc.count(g, 4)), base)
+    with vdmc.graph_create(n, np.concatenate([s, d]), np.concatenate([d, s]), undirected=True) as g:
+        np.testing.assert_array_equal(to_numpy_u64(vdmc.count(g, 4)), base)
+    perm = np.random.default_rng(3).permutation(n).astype(np.int32)
+    with vdmc.graph_create(n, perm[s], perm[d], undirected=True) as g:
+        np.testing.assert_array_equal(to_numpy_u64(vdmc.count(g, 4))[perm], base)
+    # per-edge (directed), k=3: relabelled edge rows match
+    m, s2, d2 = synth.chung_lu(5000, 4.0, 2.4, 12, reciprocity=0.3)
+    with vdmc.graph_create(m, s2, d2) as g:
+        u, v, _ = g.edges()
+        e0 = to_numpy_u64(vdmc.count_edges(g, 3))
+    perm = np.random.default_rng(4).permutation(m).astype(np.int32)
+    with vdmc.graph_create(m, perm[s2], perm[d2]) as g:
+        u2, v2, _ = g.edges()
+        e1 = to_numpy_u64(vdmc.count_edges(g, 3))
+    row = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(u2, v2))}
+    idx = np.array([row[(min(int(perm[a]), int(perm[b])), max(int(perm[a]), int(perm[b])))] for a, b in zip(u, v)])
+    np.testing.assert_array_equal(e1[idx], e0)
