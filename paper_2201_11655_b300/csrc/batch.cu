@@ -126,6 +126,7 @@ void free_union(vdmc_graph *U, cudaStream_t fs) {
     vdmc_free(U->status, fs);
     vdmc_free(U->racc, fs);
     vdmc_free(U->d3acc, fs);
+    vdmc_free(U->d3w, fs);
     vdmc_free(U->stats, fs);
     vdmc_hub_free(U, fs);
     if (U->side) cudaStreamDestroy(U->side);

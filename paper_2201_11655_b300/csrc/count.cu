@@ -897,10 +897,12 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
             g->d3_mode = hmx < (1ull << 32) ? 1 : 2;
         }
         if (!g->d3acc) VDMC_CUDA_TRY(vdmc_malloc(&g->d3acc, sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS, s));
+        if (!g->d3w) VDMC_CUDA_TRY(vdmc_malloc(&g->d3w, sizeof(uint64_t) * (size_t)g->n * 9, s));
         d3 = g->d3acc;
         narrow = g->d3_mode == 1 && sch.d3_bits != 64;
         const size_t width = narrow ? sizeof(uint32_t) : sizeof(uint64_t);
         VDMC_CUDA_TRY(cudaMemsetAsync(d3, 0, width * (size_t)g->n * VDMC_D3_COLS, s));
+        VDMC_CUDA_TRY(cudaMemsetAsync(g->d3w, 0, width * (size_t)g->n * 9, s));
     }
     const uint8_t *lut = nullptr;
     VDMC_CUDA_TRY(device_lut(k, &lut));
@@ -910,7 +912,8 @@ vdmc_status vdmc_count_internal(vdmc_graph *g, int k, int32_t lo, int32_t hi, ui
         // with the warp kernel; the caller's stream waits for both
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
         VDMC_CUDA_TRY(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
-        vdmc_status st = vdmc_hub_launch(g, k, acc, d3, narrow ? 1 : 0, lut, lo, hi, sch.hub_blocks_per_sm,
+        vdmc_status st = vdmc_hub_launch(g, k, acc, d3, narrow ? 1 : 0, d3 ? g->d3w : nullptr, lut, lo, hi,
+                                          sch.hub_blocks_per_sm,
                                           sch.hub_split, sch.hub_split_roots, sch.hub_warps, g->side);
         if (st != VDMC_OK) return st;
         VDMC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side));

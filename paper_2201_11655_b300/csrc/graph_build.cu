@@ -225,6 +225,7 @@ void free_graph_buffers(vdmc_graph *g) {
     vdmc_batch_plan_free(g);
     vdmc_free(g->racc, fs);
     vdmc_free(g->d3acc, fs);
+    vdmc_free(g->d3w, fs);
     vdmc_free(g->stats, fs);
     vdmc_free(g->ebase, fs);
     vdmc_free(g->erow, fs);
@@ -484,6 +485,7 @@ extern "C" vdmc_status vdmc_graph_info(const vdmc_graph *g, vdmc_graph_info_t *i
     info->device_bytes += (int64_t)g->hub_scratch_bytes;
     if (g->racc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_MAX_CLASSES);
     if (g->d3acc) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * VDMC_D3_COLS);
+    if (g->d3w) info->device_bytes += (int64_t)(sizeof(uint64_t) * (size_t)g->n * 9);
     return VDMC_OK;
 }
 

@@ -68,6 +68,7 @@ struct HubArgs {
     uint64_t *out;
     unsigned long long *d3;     // k = 4: n * VDMC_D3_COLS depth-3 credits (rank space)
     int d3_narrow;              // 1: the credits are 32-bit words (no vertex can reach 2^32 of them)
+    unsigned long long *d3w;    // k = 4: n * 9 type counts per vertex, spread to its neighbours after the kernel
     unsigned long long *stats;  // [1] sets of hub roots, [2] of those visited one by one (or nullptr)
     const uint8_t *lut_g;
     const int32_t *hubs;
@@ -97,6 +98,16 @@ struct HubArgs {
 };
 
 __device__ __forceinline__ uint32_t swapf(uint32_t f) { return ((f & 1u) << 1) | (f >> 1); }
+
+// add (or subtract) v to word i of a depth-3 array, in the counters' width;
+// sums are exact modulo that width, so a subtraction ahead of the addition it
+// cancels is harmless.  The result is not used: a reduction, not a wait.
+__device__ __forceinline__ void d3_add(unsigned long long *a, int narrow, int64_t i, uint32_t v, bool neg) {
+    if (narrow)
+        atomicAdd(reinterpret_cast<unsigned int *>(a) + i, neg ? 0u - v : v);
+    else
+        atomicAdd(a + i, neg ? 0ull - (unsigned long long)v : (unsigned long long)v);
+}
 
 // canonical index of an H-edge (y,z): colours cy, cz (1..3), flag f = h(y,z)
 __device__ __forceinline__ int etype(uint32_t cy, uint32_t cz, uint32_t f) {
@@ -1022,7 +1033,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                 c0 = __shfl_sync(0xffffffffu, c0, 0);
                 if (c0 >= tcount) break;
                 const int32_t t = lane < csz ? c0 + lane : tcount;
-                uint32_t b = 0u, nzm = 0u;
+                uint32_t b = 0u, nzm = 0u, nzd = 0u;  // nzd: types whose depth-3 credits the walk issues
                 int64_t be = 0;
                 int32_t len = 0, o0 = 0, o1 = 0;
                 if (t < tcount) b = (uint32_t)touched[t];
@@ -1071,6 +1082,43 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                                 const uint32_t cls = lut[mask4(c1, (uint32_t)(t2 / 3 + 1), 0u, 0u, h1, (uint32_t)(t2 % 3 + 1))];
                                 gadd(S, b, cls, cnt, C);
                                 sadd(hD, cls, cnt);
+                            }
+                        }
+                        // S4 credits of the depth-3 vertices c: the neighbours of b in
+                        // its upper row outside P, each by (type of x, h(b, c)).  Either
+                        // the walk below adds b's type counts at every such c, or -- when
+                        // the rest of b's row (ranks below r, members of P) is the
+                        // shorter part -- they go once to d3w[b], d3_spread adds d3w[b]
+                        // at every neighbour of b after the kernel, and the neighbours
+                        // that must not have them are subtracted here.
+                        nzd = nzm;
+                        const int64_t ub = be - len;
+                        const int32_t lower = (int32_t)(ub - bb), npn = o1 - o0;
+                        if (nzm && 1 + npn + lower < len - npn) {
+                            nzd = 0u;
+                            for (uint32_t m1 = nzm; m1; m1 &= m1 - 1u) {
+                                const int t1 = __ffs(m1) - 1;
+                                d3_add(A.d3w, A.d3_narrow, (int64_t)b * 9 + t1, sq[lane * 9 + t1], false);
+                            }
+                            for (int32_t x = o0; x < o1; x++) {
+                                const uint32_t ex = nplist[x];
+                                const uint32_t xv = __ldg(P + (ex >> 2)) >> 2, hbx = swapf(ex & 3u);  // h(b, x)
+                                if (!in_bounds(g, xv < (uint32_t)g.n && hbx != 0u)) continue;
+                                for (uint32_t m1 = nzm; m1; m1 &= m1 - 1u) {
+                                    const int t1 = __ffs(m1) - 1;
+                                    d3_add(A.d3, A.d3_narrow, (int64_t)xv * VDMC_D3_COLS + d3col[t1 * 3 + hbx - 1],
+                                           sq[lane * 9 + t1], true);
+                                }
+                            }
+                            for (int64_t j = bb; j < ub; j++) {
+                                const uint32_t ent = __ldg(g.col + j);
+                                const uint32_t cv = ent >> 2, gg = ent & 3u;
+                                if (!in_bounds(g, cv < (uint32_t)g.n && gg != 0u)) continue;
+                                for (uint32_t m1 = nzm; m1; m1 &= m1 - 1u) {
+                                    const int t1 = __ffs(m1) - 1;
+                                    d3_add(A.d3, A.d3_narrow, (int64_t)cv * VDMC_D3_COLS + d3col[t1 * 3 + gg - 1],
+                                           sq[lane * 9 + t1], true);
+                                }
                             }
                         }
                     }
@@ -1156,7 +1204,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                     wn = owner(j + 32);
                     entn = entry(j + 32, wn);
                     const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
-                    const uint32_t nzo = __shfl_sync(0xffffffffu, nzm, w);
+                    const uint32_t nzo = __shfl_sync(0xffffffffu, nzd, w);
                     const uint32_t c = ent >> 2, gg = ent & 3u;
                     bool cand = false;
                     if (j < total && !in_P(c)) {
@@ -1169,11 +1217,8 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                                     // a reduction: its result is not needed, so the warp
                                     // does not wait for it (a 32-bit add with a carry
                                     // check would make it wait on every entry)
-                                    const int64_t di = (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1];
-                                    if (A.d3_narrow)
-                                        atomicAdd(reinterpret_cast<unsigned int *>(A.d3) + di, sq[w * 9 + k]);
-                                    else
-                                        atomicAdd(A.d3 + di, (unsigned long long)sq[w * 9 + k]);
+                                    d3_add(A.d3, A.d3_narrow, (int64_t)c * VDMC_D3_COLS + d3col[k * 3 + gg - 1],
+                                           sq[w * 9 + k], false);
                                 }
                         }
                         cand = c > bo && claimed(c);  // else counted from c, or no P neighbour
@@ -1223,6 +1268,60 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
             }
         }
         reset_slot<HUB_THREADS>(posmap, qcnt, touched, P, L, tcount, pbits, sbits, tbits);
+    }
+}
+
+// After the root-per-CTA kernel (k = 4): every vertex c adds the type counts
+// d3w[b] of each neighbour b to its depth-3 columns, by (type, h(b, c)) -- the
+// second half of the per-vertex route of phase 6 (the kernel has already
+// subtracted the neighbours of b that are not at depth 3).  One warp per vertex,
+// lanes over its row; plain adds, since nothing else writes d3 meanwhile.
+__global__ void d3_spread(const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ col, int32_t n,
+                          const unsigned long long *__restrict__ d3w, int narrow, const uint8_t *__restrict__ lut,
+                          unsigned long long *__restrict__ d3) {
+    __shared__ uint8_t d3c[27];
+    if (threadIdx.x < 27) {
+        int cls = 0;
+        d3c[threadIdx.x] = (uint8_t)min(d3_column(lut, threadIdx.x, &cls), VDMC_D3_COLS - 1);
+    }
+    __syncthreads();
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(d3w);
+    unsigned long long acc[VDMC_D3_COLS];
+#pragma unroll
+    for (int q = 0; q < VDMC_D3_COLS; q++) acc[q] = 0ull;
+    bool any = false;
+    for (int64_t p = __ldg(rowptr + c) + lane; p < __ldg(rowptr + c + 1); p += 32) {
+        const uint32_t ent = __ldg(col + p);
+        const uint32_t b = ent >> 2, hbc = swapf(ent & 3u);  // c's row holds h(c, b)
+        if (b >= (uint32_t)n || hbc == 0u) continue;
+        for (int k = 0; k < 9; k++) {
+            const unsigned long long v = narrow ? (unsigned long long)__ldg(w32 + (int64_t)b * 9 + k)
+                                                : __ldg(d3w + (int64_t)b * 9 + k);
+            if (!v) continue;
+            any = true;
+            const uint32_t q0 = d3c[k * 3 + hbc - 1];
+#pragma unroll
+            for (int q = 0; q < VDMC_D3_COLS; q++) acc[q] += q == (int)q0 ? v : 0ull;
+        }
+    }
+    if (!__any_sync(0xffffffffu, any)) return;
+    unsigned long long mine = 0ull;
+#pragma unroll
+    for (int q = 0; q < VDMC_D3_COLS; q++) {
+        unsigned long long v = acc[q];
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == q) mine = v;
+    }
+    if (lane < VDMC_D3_COLS && mine) {
+        if (narrow) {
+            uint32_t *d = reinterpret_cast<uint32_t *>(d3) + c * VDMC_D3_COLS + lane;
+            *d += (uint32_t)mine;
+        } else {
+            d3[c * VDMC_D3_COLS + lane] += mine;
+        }
     }
 }
 
@@ -1399,7 +1498,8 @@ cudaError_t launch_hub(int slots, size_t dsmem, const HubArgs &A, cudaStream_t s
     return cudaGetLastError();
 }
 
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, const uint8_t *lut,
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, uint64_t *d3w,
+                            const uint8_t *lut,
                             int32_t lo,
                             int32_t hi, int blocks_per_sm, int split, int split_roots, int warps, cudaStream_t s) {
     warps = warps == 32 ? 32 : 16;
@@ -1449,6 +1549,7 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, i
     A.out = out;
     A.d3 = (unsigned long long *)d3;
     A.d3_narrow = d3_narrow;
+    A.d3w = (unsigned long long *)d3w;
     A.stats = g->stats;
     A.lut_g = lut;
     A.hubs = g->hubs;
@@ -1486,6 +1587,11 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, i
     if (nsplit > 0) {
         split_finish<<<(unsigned)nsplit, 256, 0, s>>>(A.split_acc, g->hubs, nsplit, C, k == 3 ? 2ull : 3ull, g->n, out,
                                                       g->stats);
+        VDMC_CUDA_TRY(cudaGetLastError());
+    }
+    if (k == 4 && d3 && d3w) {
+        d3_spread<<<(unsigned)(((int64_t)g->n * 32 + 255) / 256), 256, 0, s>>>(g->rowptr, g->col, g->n, A.d3w, d3_narrow,
+                                                                             lut, A.d3);
         VDMC_CUDA_TRY(cudaGetLastError());
     }
     return VDMC_OK;

@@ -66,6 +66,7 @@ struct vdmc_graph {
     void *batch_plan;            // cached plan of vdmc_count_batch calls led by this graph
     uint64_t *racc;              // rank-space credit accumulator, n * VDMC_MAX_CLASSES
     uint64_t *d3acc;             // k = 4 depth-3 credits of the root-per-CTA kernel, n * VDMC_D3_COLS (rank space)
+    uint64_t *d3w;               // k = 4 per-vertex type counts spread to the neighbours' depth-3 credits, n * 9
     int d3_mode;                 // 0 unknown, 1: 32-bit depth-3 credits suffice (d3_bound), 2: 64-bit
     unsigned long long *stats;   // VDMC_NSTATS counters of the last count (vdmc_count_stats)
     int undirected;              // VDMC_GRAPH_UNDIRECTED: every edge carries flags 3, output in undirected classes
@@ -172,7 +173,8 @@ void vdmc_current_schedule(vdmc_schedule_t *s);
 
 // ---- root-per-CTA kernel (hub.cu) ----
 vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s);
-vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, const uint8_t *lut,
+vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, int d3_narrow, uint64_t *d3w,
+                            const uint8_t *lut,
                             int32_t lo, int32_t hi, int blocks_per_sm, int split, int split_roots, int warps,
                             cudaStream_t s);
 void vdmc_hub_free(vdmc_graph *g, cudaStream_t s);
