@@ -534,8 +534,8 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     model = g.work_model(k)
     roofline = roofline_of(model, ms, peak, peak_kind,
-                           "vdmc_count: hub_kernel<%d, %d warps> (root-per-CTA) overlapped with count_kernel<%d> "
-                           "(warp-per-task), timed together" % (k, vdmc.get_schedule()["hub_warps"] or 16, k),
+                           "vdmc_count: hub_kernel<%d, %s warps> (root-per-CTA) overlapped with count_kernel<%d> "
+                           "(warp-per-task), timed together" % (k, vdmc.get_schedule()["hub_warps"] or "16 or 32", k),
                            None, load_traffic(k))
 
     cpu = None

@@ -90,9 +90,10 @@ typedef struct {
                                    takes a share of its members and second-hop
                                    vertices */
     int32_t hub_split_roots;    /* how many of the largest roots are split (>= 0) */
-    int32_t hub_warps;          /* root-per-CTA kernel: warps per CTA, 16 or 32
-                                   (0 = 16); 32 unless set (more warps hide more
-                                   of the kernel's load latency) */
+    int32_t hub_warps;          /* root-per-CTA kernel: warps per CTA, 16 or 32;
+                                   0 (the default) = 32 when the graph's largest
+                                   hub root has at least 640 higher-rank
+                                   neighbours, else 16 */
     int32_t d3_bits;            /* root-per-CTA kernel, k = 4: width of the depth-3
                                    credit counters; 0 = 32 bits when a per-graph
                                    bound shows that no vertex can reach 2^32 of

@@ -41,7 +41,7 @@
 
 namespace {
 
-vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, 32, 0};
+vdmc_schedule_t g_sched = {16, 8, 0, 64, 1, 1, 0, 0, 0};
 std::mutex g_sched_mu;
 
 struct DevLut {

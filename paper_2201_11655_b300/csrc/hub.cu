@@ -1502,6 +1502,9 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, i
                             const uint8_t *lut,
                             int32_t lo,
                             int32_t hi, int blocks_per_sm, int split, int split_roots, int warps, cudaStream_t s) {
+    // 0: by the largest root -- 32 warps hide more of a long root's load
+    // latency, 16 cost less per launch for graphs of small roots
+    if (warps == 0) warps = g->hub_lmax >= VDMC_HUB_WARPS32_MIN_L ? 32 : 16;
     warps = warps == 32 ? 32 : 16;
     if (g->nhubs <= 0) return VDMC_OK;
     int dev = 0, sms = 0;

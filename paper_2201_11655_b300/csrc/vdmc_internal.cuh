@@ -92,6 +92,10 @@ constexpr int VDMC_NSTATS = 4;
 // 27 types in 15 classes (a path and its reverse are isomorphic); one column
 // per class, 16 columns = one 128-byte line per vertex.
 constexpr int VDMC_D3_COLS = 16;
+// hub_warps = 0: 32-warp root-per-CTA CTAs when the largest hub root has at
+// least this many higher-rank neighbours (measured: 32 warps faster from ~830,
+// slower at ~500 and below)
+constexpr int64_t VDMC_HUB_WARPS32_MIN_L = 640;
 
 // ---- device memory ----
 // Graph-owned device memory is stream-ordered (cudaMallocAsync on the stream
