@@ -94,6 +94,7 @@ struct HubArgs {
     int32_t pbits_words;  // > 0: membership of P as a bitmap in shared memory
     int32_t *npoff;    // tcap + 1 per slot: offsets of the NP lists
     uint32_t *nplist;  // npcap per slot: (position << 2) | h(x, b)
+    longlong2 *qrow;   // k = 4, tcap per slot: row end of each Q vertex, (entries below r << 32) | entries above r
     int64_t tcap, hcap, lmax, npcap;
 };
 
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
     };
     auto claimed = [&](uint32_t u) -> bool { return ((__ldcg(tbits + (u >> 5)) >> (u & 31u)) & 1u) != 0u; };
     uint32_t *nplist = A.nplist + slot * A.npcap;
+    longlong2 *qrow = A.qrow + slot * A.tcap;
     unsigned long long *hv = whist[warp];
     const Hist64 hvh = hist64(hv, C), hP = hist64(rootP, C), hD = hist64(rootD, C);
     const Hist64 hE = hist64(Etype, 27), hW = hist64(Wtot, 9);
@@ -545,6 +547,9 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                         be = __ldg(g.rowptr + b + 1);
                         len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
                         nb0 = npoff[t];
+                        // b's row end and the lengths of its parts above and below r,
+                        // for phase 6 (spares it the row pointers and the search)
+                        qrow[t] = make_longlong2(be, (long long)((uint64_t)(be - len - bb) << 32 | (uint32_t)len));
                     }
                     srun[lane] = 0u;
                     swq[lane * 3 + 0] = swq[lane * 3 + 1] = swq[lane * 3 + 2] = 0u;
@@ -1038,9 +1043,18 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                 int32_t len = 0, o0 = 0, o1 = 0;
                 if (t < tcount) b = (uint32_t)touched[t];
                 if (t < tcount && (int32_t)(b % (uint32_t)nparts) == part) {
-                    const int64_t bb = __ldg(g.rowptr + b);
-                    be = __ldg(g.rowptr + b + 1);
-                    len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
+                    int64_t bb;
+                    if constexpr (K == 4) {
+                        // row end and part lengths saved by phase 4
+                        const longlong2 qr = __ldcg(qrow + t);
+                        be = qr.x;
+                        len = (int32_t)(uint32_t)qr.y;
+                        bb = be - len - (int64_t)((uint64_t)qr.y >> 32);
+                    } else {
+                        bb = __ldg(g.rowptr + b);
+                        be = __ldg(g.rowptr + b + 1);
+                        len = (int32_t)(be - upper_row(g.col, bb, be, (uint32_t)r));
+                    }
                     o0 = npoff[t];
                     o1 = npoff[t + 1];
 #pragma unroll
@@ -1121,6 +1135,9 @@ __global__ void __launch_bounds__(W * 32, 1) hub_kernel(const HubArgs args) {
                                 }
                             }
                         }
+                        // without depth-3 credits to issue, the walk only looks for
+                        // triangle candidates c > b: the part of the row above b
+                        if (nzd == 0u) len = (int32_t)(be - max(ub, __ldg(g.pbeg + b)));
                     }
                 }
                 if (K == 3) continue;
@@ -1458,7 +1475,7 @@ vdmc_status vdmc_build_hubs(vdmc_graph *g, int32_t min_l, cudaStream_t s) {
 namespace {
 
 struct HubLayout {
-    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npoff, nplist, tbits, total;
+    size_t posmap, qcnt, wq, touched, hptr, hlist, hcx, wx, htx, npoff, nplist, qrow, tbits, total;
 };
 
 HubLayout hub_layout(const vdmc_graph *g, int slots) {
@@ -1476,6 +1493,7 @@ HubLayout hub_layout(const vdmc_graph *g, int slots) {
     L.htx = o; o += align256(S * lm * 9 * 4);
     L.npoff = o; o += align256(S * (t + 1) * 4);
     L.nplist = o; o += align256(S * (size_t)g->hub_npcap * 4);
+    L.qrow = o; o += align256(S * t * 16);
     L.tbits = o; o += align256(S * ((n + 31) / 32) * 4);
     L.total = o;
     return L;
@@ -1575,6 +1593,7 @@ vdmc_status vdmc_hub_launch(vdmc_graph *g, int k, uint64_t *out, uint64_t *d3, i
     A.npoff = (int32_t *)(base + L.npoff);
     A.nplist = (uint32_t *)(base + L.nplist);
     A.npcap = g->hub_npcap;
+    A.qrow = (longlong2 *)(base + L.qrow);
     A.tbits = (uint32_t *)(base + L.tbits);
     const int64_t words = ((int64_t)g->n + 31) / 32;
     A.pbits_words = words <= hub_smem_bits_max_words(warps) ? (int32_t)words : 0;
