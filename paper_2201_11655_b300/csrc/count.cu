@@ -245,6 +245,46 @@ __device__ __forceinline__ uint32_t view_find(const Csr &g, const View &v, uint3
     return 0u;
 }
 
+// Per-warp open-addressing table of the k = 4 flattened walk (linear
+// probing, 256 slots, at most 64 + 128 keys, so a probe always ends at an
+// empty slot): word = (vertex << 4) | bits, vertex ids below 2^28.
+constexpr int HT_SLOTS = 256;
+constexpr uint32_t HT_EMPTY = 0xffffffffu;
+constexpr int32_t HT_MAX_N = 1 << 28;
+
+__device__ __forceinline__ uint32_t ht_slot(uint32_t v) { return (v * 0x9E3779B1u) >> 24; }
+
+// add `bits` to v's word, inserting v if absent (keys of one call are
+// distinct across the lanes, so no two lanes insert the same vertex)
+__device__ __forceinline__ void ht_insert(uint32_t *ht, uint32_t v, uint32_t bits) {
+    uint32_t h = ht_slot(v);
+    for (int i = 0; i < HT_SLOTS; i++, h = (h + 1u) & (HT_SLOTS - 1)) {
+        const uint32_t cur = ht[h];
+        if (cur == HT_EMPTY) {
+            const uint32_t prev = atomicCAS(ht + h, HT_EMPTY, (v << 4) | bits);
+            if (prev == HT_EMPTY) return;
+            if ((prev >> 4) == v) {
+                atomicOr(ht + h, bits);
+                return;
+            }
+        } else if ((cur >> 4) == v) {
+            atomicOr(ht + h, bits);
+            return;
+        }
+    }
+}
+
+// v's bits, 0 if absent
+__device__ __forceinline__ uint32_t ht_find(const uint32_t *ht, uint32_t v) {
+    uint32_t h = ht_slot(v);
+    for (int i = 0; i < HT_SLOTS; i++, h = (h + 1u) & (HT_SLOTS - 1)) {
+        const uint32_t cur = ht[h];
+        if (cur == HT_EMPTY) return 0u;
+        if ((cur >> 4) == v) return cur & 15u;
+    }
+    return 0u;
+}
+
 template <int K, bool EDGE>
 __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const GraphDesc *__restrict__ multi,
                                                    const Task *__restrict__ tasks, int64_t ntasks,
@@ -419,7 +459,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
                     set3(a, b, ia, -1, eb & 3u, cls);
                 }
-            } else if (!EDGE && VP.s != nullptr && a_end - a_up <= STAGE_A) {
+            } else if (!EDGE && VP.s != nullptr && a_end - a_up <= STAGE_A && G.n <= HT_MAX_N) {
                 // Flattened walk of every set with this a, lanes on consecutive
                 // (b, c) work items (short candidate lists would leave most
                 // lanes idle).  b-items: the members of P after a, then the
@@ -435,6 +475,18 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                 const int32_t la = (int32_t)(a_end - a_up);
                 const int32_t n1 = L - 1 - ia;
                 const int32_t nitems = n1 + la;
+                // Membership in N+(r) and in N(a) above r, with the flags from r
+                // and from a, in one open-addressing table: word = (vertex << 4) |
+                // (h(a, v) << 2) | h(r, v), empty = ~0.  It lives in the warp's
+                // b-histogram area (zero between b's, unused on this walk; 256 of
+                // its 2C words for at most 64 + 128 keys) and is zeroed again after.
+                uint32_t *ht = hist_b.lo;
+                for (int i = lane; i < HT_SLOTS; i += 32) ht[i] = HT_EMPTY;
+                __syncwarp();
+                for (int32_t p = lane; p < L; p += 32) ht_insert(ht, VP.s[p] >> 2, VP.s[p] & 3u);
+                __syncwarp();
+                for (int32_t x = lane; x < la; x += 32) ht_insert(ht, NA.s[x] >> 2, (NA.s[x] & 3u) << 2);
+                __syncwarp();
                 for (int32_t it0 = 0; it0 < nitems; it0 += 32) {
                     const int32_t it = it0 + lane;
                     uint32_t b = 0u, frb = 0u, fab = 0u;
@@ -446,12 +498,13 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         const uint32_t eb = inp ? VP.s[pos] : NA.s[pos];
                         b = eb >> 2;
                         bool ok = in_bounds(g, b < G.n);
+                        const uint32_t hb = ht_find(ht, b);
                         if (inp) {
                             frb = eb & 3u;
-                            fab = view_find(g, NA, b);
+                            fab = hb >> 2;
                         } else {
                             fab = eb & 3u;
-                            ok = ok && !view_find(g, VP, b);  // a member of P is not at depth 2
+                            ok = ok && (hb & 3u) == 0u;  // a member of P is not at depth 2
                         }
                         if (ok) {
                             const int64_t bb = __ldg(g.rowptr + b);
@@ -486,40 +539,42 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         const bool inpo = it0 + w < n1;
                         uint32_t c = 0u, cls = 255u;
                         if (j < total) {
-                            int32_t off = j - start;
+                            // one path for every shape: the candidate's source (a staged
+                            // list or b's row) and which memberships rule it out
+                            //   b in P:   P after b (1,1,1) | N(a) \ P (1,1,2) | N(b) \ N(a) \ P (1,1,2)
+                            //   b deeper: N(a) \ P after b (1,2,2) | N(b) \ (N(a) u P) (1,2,3)
+                            int32_t off = j - start, sidx = 0;
+                            int64_t gidx = 0;
+                            bool from_b = false, not_p = true;
                             if (inpo) {
                                 const int32_t n111 = L - 1 - poso;
-                                if (off < n111) {  // (1,1,1)
-                                    const uint32_t ec = VP.s[poso + 1 + off];
-                                    c = ec >> 2;
-                                    const uint32_t fac = view_find(g, NA, c);
-                                    const uint32_t fbc = search_row(g.col, bupo, bendo, c);
-                                    cls = lut[mask4(fra, frbo, ec & 3u, fabo, fac, fbc)];
-                                } else if ((off -= n111) < la) {  // (1,1,2), c adjacent to a
-                                    const uint32_t ec = NA.s[off];
-                                    c = ec >> 2;
-                                    if (!view_find(g, VP, c))
-                                        cls = lut[mask4(fra, frbo, 0u, fabo, ec & 3u,
-                                                        search_row(g.col, bupo, bendo, c))];
-                                } else {  // (1,1,2), c adjacent to b only
-                                    const uint32_t ec = __ldg(g.col + bupo + (off - la));
-                                    c = ec >> 2;
-                                    if (!view_find(g, VP, c) && !view_find(g, NA, c))
-                                        cls = lut[mask4(fra, frbo, 0u, fabo, 0u, ec & 3u)];
+                                if (off < n111) {
+                                    sidx = poso + 1 + off;
+                                    not_p = false;
+                                } else if ((off -= n111) < la) {
+                                    sidx = STAGE_P + off;
+                                } else {
+                                    gidx = bupo + (off - la);
+                                    from_b = true;
                                 }
                             } else {
                                 const int32_t n122 = la - poso - 1;
-                                if (off < n122) {  // (1,2,2)
-                                    const uint32_t ec = NA.s[poso + 1 + off];
-                                    c = ec >> 2;
-                                    if (!view_find(g, VP, c))
-                                        cls = lut[mask4(fra, 0u, 0u, fabo, ec & 3u, search_row(g.col, bupo, bendo, c))];
-                                } else {  // (1,2,3)
-                                    const uint32_t ec = __ldg(g.col + bupo + (off - n122));
-                                    c = ec >> 2;
-                                    if (!view_find(g, VP, c) && !view_find(g, NA, c))
-                                        cls = lut[mask4(fra, 0u, 0u, fabo, 0u, ec & 3u)];
+                                if (off < n122) {
+                                    sidx = STAGE_P + poso + 1 + off;
+                                } else {
+                                    gidx = bupo + (off - n122);
+                                    from_b = true;
                                 }
+                            }
+                            const uint32_t ec = from_b ? __ldg(g.col + gidx) : lists[sidx];
+                            c = ec >> 2;
+                            const uint32_t hc = ht_find(ht, c);
+                            const uint32_t frc = hc & 3u, fac = hc >> 2;
+                            // a candidate from b's row must be in neither list; one from N(a)
+                            // must not be in P
+                            if (!(not_p && frc != 0u) && !(from_b && fac != 0u)) {
+                                const uint32_t fbc = from_b ? (ec & 3u) : search_row(g.col, bupo, bendo, c);
+                                cls = lut[mask4(fra, inpo ? frbo : 0u, frc, fabo, fac, fbc)];
                             }
                             if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
                         }
@@ -535,6 +590,9 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         if (hit && lane == __ffs(grp) - 1) credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
                     }
                 }
+                __syncwarp();
+                for (int i = lane; i < HT_SLOTS; i += 32) ht[i] = 0u;  // the b-histogram again
+                __syncwarp();
             } else {
                 // (A1) b in P after a
                 for (int32_t ib = ia + 1; ib < L; ib++) {
