@@ -342,8 +342,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             if constexpr (EDGE) {
                 edge_set<3>(g, E, out, (uint32_t)r, a, b, 0u, ia, ib, -1, fab, 0u, 0u, cls);
             } else {
-                hinc(hist_r, cls);
-                hinc(hist_a, cls);
+                hinc(hist_a, cls);  // r gets a's totals when a is flushed
                 credit(g, out, G.new2old, b, C, cls);
             }
             nsets++;
@@ -353,8 +352,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             if constexpr (EDGE) {
                 edge_set<4>(g, E, out, (uint32_t)r, a, b, c, ia, ib, ic, fab, fac, fbc, cls);
             } else {
-                hinc(hist_r, cls);
-                hinc(hist_a, cls);
+                hinc(hist_a, cls);  // r gets a's totals when a is flushed
                 hinc(hist_b, cls);
                 credit(g, out, G.new2old, c, C, cls);
             }
@@ -422,13 +420,16 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     }
                     const bool hit = cls != 255u;
                     if (hit) {
-                        hinc(hist_r, cls);
                         credit(g, out, G.new2old, b, C, cls);
                         nsets++;
                     }
+                    // a's and r's credits once per group of lanes holding the same (a, class)
                     const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
                     const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                    if (hit && lane == __ffs(grp) - 1) credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
+                    if (hit && lane == __ffs(grp) - 1) {
+                        credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
+                        hadd(hist_r, cls, (unsigned long long)__popc(grp));
+                    }
                 }
             }
         } else
@@ -580,14 +581,17 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         }
                         const bool hit = cls != 255u;
                         if (hit) {
-                            hinc(hist_r, cls);
-                            hinc(hist_a, cls);
                             credit(g, out, G.new2old, c, C, cls);
                             nsets++;
                         }
+                        // b's and a's credits once per group of lanes holding the same
+                        // (b, class); r gets a's totals when a is flushed
                         const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
                         const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                        if (hit && lane == __ffs(grp) - 1) credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
+                        if (hit && lane == __ffs(grp) - 1) {
+                            credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
+                            hadd(hist_a, cls, (unsigned long long)__popc(grp));
+                        }
                     }
                 }
                 __syncwarp();
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     if (!EDGE) flush_hist(g, hist_b, C, out, row_of(G.new2old, b), lane);
                 }
             }
-            if (!EDGE) flush_hist(g, hist_a, C, out, row_of(G.new2old, a), lane);
+            if (!EDGE) flush_hist_into(g, hist_a, hist_r, C, out, row_of(G.new2old, a), lane);
         }
         if (!EDGE) flush_hist(g, hist_r, C, out, row_of(G.new2old, r), lane);
     }
