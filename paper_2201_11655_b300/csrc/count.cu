@@ -245,6 +245,26 @@ __device__ __forceinline__ uint32_t view_find(const Csr &g, const View &v, uint3
     return 0u;
 }
 
+// flush h to row orig and add its counts to the warp's histogram into
+// (each lane owns its columns of both, so plain adds)
+__device__ __forceinline__ void flush_hist_into(const Csr &g, const Hist64 &h, const Hist64 &into, int C,
+                                                uint64_t *out, int32_t orig, int lane) {
+    __syncwarp();
+    const bool ok = in_bounds(g, orig >= 0 && orig < g.n);
+    for (int c = lane; c < C; c += 32) {
+        const unsigned long long v = hget(h, c);
+        if (v) {
+            if (ok) atomicAdd((unsigned long long *)&out[(int64_t)orig * C + c], v);
+            const unsigned long long t = hget(into, c) + v;
+            into.lo[c] = (uint32_t)t;
+            into.hi[c] = (uint32_t)(t >> 32);
+            h.lo[c] = 0u;
+            h.hi[c] = 0u;
+        }
+    }
+    __syncwarp();
+}
+
 // Per-warp open-addressing table of the k = 4 flattened walk (linear
 // probing, 256 slots, at most 64 + 128 keys, so a probe always ends at an
 // empty slot): word = (vertex << 4) | bits, vertex ids below 2^28.
