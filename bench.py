@@ -108,6 +108,23 @@ def load_traffic(k):
     return None
 
 
+def load_traffic_full(k):
+    """The committed one-launch ncu record of the root-per-CTA kernel on the
+    full-size workload itself (profiles/traffic_full_size.json: DRAM bytes read
+    + written, a one-pass capture), if it was taken on the current kernel
+    sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_full_size.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        e = rec.get("k%d" % k)
+        if e and e.get("kernel_hash") == kernel_source_hash():
+            return dict(e, ratio_to_algorithmic=e["dram_bytes_per_launch"] / e["algorithmic_bytes_of_count"])
+    except Exception:
+        pass
+    return None
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -537,6 +554,13 @@ def run_ours(args):
                            "vdmc_count: hub_kernel<%d, %s warps> (root-per-CTA) overlapped with count_kernel<%d> "
                            "(warp-per-task), timed together" % (k, vdmc.get_schedule()["hub_warps"] or "16 or 32", k),
                            None, load_traffic(k))
+    # traffic: DRAM bytes of one root-per-CTA launch of this very workload and
+    # schedule, when the committed full-size record matches the kernel sources
+    # (else null)
+    full = load_traffic_full(k) if args.workload == DEFAULT_WORKLOAD and not args.no_tuned else None
+    if full:
+        roofline["traffic"] = full["dram_bytes_per_launch"]
+        roofline["traffic_full_size"] = full
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -47,3 +47,16 @@ def test_traffic_record_only_for_current_kernel(tmp_path, monkeypatch):
     else:
         assert got is None
     assert bench.load_traffic(3) is None
+
+
+def test_full_size_traffic_record_only_for_current_kernel():
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic_full_size.json")))
+    e = rec["k4"]
+    assert e["workload"] == bench.DEFAULT_WORKLOAD
+    assert e["dram_bytes_per_launch"] == e["dram_read"] + e["dram_write"]
+    got = bench.load_traffic_full(4)
+    if e["kernel_hash"] == bench.kernel_source_hash():
+        assert got is not None and got["dram_bytes_per_launch"] == e["dram_bytes_per_launch"]
+    else:
+        assert got is None
+    assert bench.load_traffic_full(3) is None

@@ -161,6 +161,64 @@ def test_schedules_do_not_change_results():
         vdmc.set_schedule(**old)
 
 
+
+def _full_table_graph(seed):
+    """A root r with exactly 64 higher-rank neighbours (the most the warp kernel
+    stages) and, among them, a with 128 neighbours of higher rank than r, none
+    in N+(r), and a2 with 120 outside N+(r) and 8 inside: the flattened k = 4
+    walk's membership table then holds 192 and 184 keys in its 256 slots.
+    66 hubs of larger degree (131 private leaves each) take r's lower ranks."""
+    rng = np.random.default_rng(seed)
+    r, P = 0, list(range(1, 65))
+    a, a2 = 1, 2
+    nxt = 65
+    A = list(range(nxt, nxt + 128)); nxt += 128
+    A2 = list(range(nxt, nxt + 120)); nxt += 120
+    hubs = list(range(nxt, nxt + 66)); nxt += 66
+    edges = [(r, x) for x in P] + [(r, h) for h in hubs] + [(a, y) for y in A] + [(a2, y) for y in A2]
+    edges += [(a2, x) for x in P[10:18]]
+    for h in hubs:
+        edges += [(h, nxt + i) for i in range(131)]
+        nxt += 131
+    # short paths among the depth-1 and depth-2 vertices (degrees stay far below r's 130)
+    for _ in range(150):
+        u, v = rng.choice(P[2:] + A + A2, 2, replace=False)
+        edges.append((int(u), int(v)))
+    src, dst = [], []
+    for u, v in edges:
+        if u == v:
+            continue
+        if rng.random() < 0.5:
+            u, v = v, u
+        src.append(u); dst.append(v)
+        if rng.random() < 0.2:
+            src.append(v); dst.append(u)
+    return nxt, np.array(src, np.int32), np.array(dst, np.int32)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_warp_kernel_membership_table_at_capacity(seed):
+    from paper_2201_11655_b300 import vdmc
+    n, s, d = _full_table_graph(seed)
+    with vdmc.graph_create(n, s, d) as g:
+        rowptr, col, new2old = g.export_csr()
+    old2new = np.empty(n, np.int64)
+    old2new[new2old] = np.arange(n)
+    rr = int(old2new[0])
+    ranks = (col[rowptr[rr]:rowptr[rr + 1]] >> 2).astype(np.int64)
+    assert int((ranks > rr).sum()) == 64            # N+(r): the staging limit
+    for v in (1, 2):                                # a, a2: 128 neighbours above r
+        rv = int(old2new[v])
+        rk = (col[rowptr[rv]:rowptr[rv + 1]] >> 2).astype(np.int64)
+        assert rv > rr and int((rk > rr).sum()) == 128
+    old = vdmc.get_schedule()
+    try:
+        vdmc.set_schedule(hub_min_l=0)              # every root through the warp kernel
+        check(n, s, d)
+    finally:
+        vdmc.set_schedule(**old)
+
+
 _SPLIT_GRAPH = {}
 
 
