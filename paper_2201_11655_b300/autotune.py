@@ -124,7 +124,8 @@ def main():
     p.add_argument("--reps", type=int, default=1)
     p.add_argument("--out", default=TUNED_PATH)
     p.add_argument("--hub-min-l", default=None, help="comma list: restrict stage 1 to these values")
-    p.add_argument("--skip-stage2", action="store_true")
+    p.add_argument("--skip-stage2", action="store_true", help="skip the warp-kernel knobs (stage 2)")
+    p.add_argument("--skip-stage3", action="store_true", help="skip the root split and CTA size (stage 3)")
     a = p.parse_args()
     vdmc.load()
     if a.batch:
@@ -141,7 +142,7 @@ def main():
         keep = {int(x) for x in a.hub_min_l.split(",")}
         stage1 = [c for c in STAGE1 if c["hub_min_l"] in keep]
     best, ms, timings = tune(g, a.k, stage1=stage1, stage2=[] if a.skip_stage2 else STAGE2,
-                             stage3=[] if a.skip_stage2 else STAGE3, reps=a.reps)
+                             stage3=[] if a.skip_stage3 else STAGE3, reps=a.reps)
     key = "k%d/%s" % (a.k, bucket(n, m))
     save_tuned(key, best, ms, {"workload": name, "n": n, "m": m, "timings_ms": timings,
                                "tuned_seconds": round(time.time() - t0, 1)}, a.out)
