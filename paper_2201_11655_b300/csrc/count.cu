@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                 // (h(a, v) << 2) | h(r, v), empty = ~0.  It lives in the warp's
                 // b-histogram area (zero between b's, unused on this walk; 256 of
                 // its 2C words for at most 64 + 128 keys) and is zeroed again after.
+                static_assert(K == 3 || 2 * C >= HT_SLOTS, "the table must fit the b-histogram area");
                 uint32_t *ht = hist_b.lo;
                 for (int i = lane; i < HT_SLOTS; i += 32) ht[i] = HT_EMPTY;
                 __syncwarp();
