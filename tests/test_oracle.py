@@ -150,12 +150,13 @@ def test_csr_example_k3_hand_worked():
     np.testing.assert_array_equal(out, want)
     out4, found4 = O.count(4, s, d, 4)
     assert found4 == 1
-    # the whole graph is one 4-set; its class is the canonical form of its
-    # own index under the identity order
-    idx = int("".join("1" if (i, j) in arcs else "0"
-                      for i in range(4) for j in range(4) if i != j), 2)
-    c = col_of(4, O.canonical_index(4, idx))
-    assert (out4[:, c] == 1).all() and out4.sum() == 4
+    # The whole graph is one 4-set.  Its minimum index, by hand: the first
+    # (most significant) row wants no out-arc -- only vertex 1 has none -> 000;
+    # the second wants no arc to vertex 1 -- only vertex 2 -> its arcs to the
+    # last two positions: 3 before 0 makes them 0, 1 -> 001; then vertex 3
+    # (arcs to 1 and 2, not to 0) -> 110; vertex 0 (arcs to all) -> 111:
+    # 000 001 110 111 = 119.
+    assert (out4[:, col_of(4, 119)] == 1).all() and out4.sum() == 4
 
 
 def _arcs(pairs):
@@ -210,8 +211,11 @@ def test_transitive_tournament():
     o3, _ = O.count(n, s, d, 3)
     o4, _ = O.count(n, s, d, 4)
     assert (o3[:, col_of(3, 11)] == math.comb(n - 1, 2)).all() and o3.sum() == 3 * math.comb(n, 3)
-    c4 = int(np.nonzero(o4[0])[0][0])
-    assert (o4[:, c4] == math.comb(n - 1, 3)).all() and o4.sum() == 4 * math.comb(n, 4)
+    # every 4-set is a transitive tournament; its minimum index, by hand: the
+    # sink first (row 000), then the vertex beating only the sink (100), then
+    # the one beating those two (110), the source last (111): 000 100 110 111
+    # = 311
+    assert (o4[:, col_of(4, 311)] == math.comb(n - 1, 3)).all() and o4.sum() == 4 * math.comb(n, 4)
 
 
 # ------------------------------------------------------------ invariants --
