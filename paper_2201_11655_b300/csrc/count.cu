@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             nsets++;
         };
 
-        if (K == 3 && !EDGE && VP.s != nullptr) {
+        if (K == 3 && VP.s != nullptr) {
             // k = 3 flattened over the task's depth-1 vertices a: a-items (32
             // at a time, one per lane), each with the candidates b in P after
             // a (star) and b in N(a) above r, not in P (path); lanes take
@@ -424,31 +424,41 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
                     const int64_t aupo = __shfl_sync(0xffffffffu, a_up, w);
                     const int64_t aendo = __shfl_sync(0xffffffffu, a_end, w);
-                    uint32_t b = 0u, cls = 255u;
+                    uint32_t b = 0u, cls = 255u, fab = 0u;
+                    int32_t ib = -1;  // position of b in N+(r) (star), else -1
                     if (j < total) {
                         const int32_t off = j - start, nstar = L - 1 - iao;
                         if (off < nstar) {  // star: b in P after a
-                            const uint32_t eb = VP.s[iao + 1 + off];
+                            ib = iao + 1 + off;
+                            const uint32_t eb = VP.s[ib];
                             b = eb >> 2;
-                            cls = lut[mask3(frao, eb & 3u, search_row(g.col, aupo, aendo, b))];
+                            fab = search_row(g.col, aupo, aendo, b);
+                            cls = lut[mask3(frao, eb & 3u, fab)];
                         } else {  // path: b in N(a) \ N(r)
                             const uint32_t eb = __ldg(g.col + aupo + (off - nstar));
                             b = eb >> 2;
-                            if (!view_find(g, VP, b)) cls = lut[mask3(frao, 0u, eb & 3u)];
+                            fab = eb & 3u;
+                            if (!view_find(g, VP, b)) cls = lut[mask3(frao, 0u, fab)];
                         }
                         if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
                     }
                     const bool hit = cls != 255u;
                     if (hit) {
-                        credit(g, out, G.new2old, b, C, cls);
+                        if constexpr (EDGE) {
+                            edge_set<3>(g, E, out, (uint32_t)r, ao, b, 0u, iao, ib, -1, fab, 0u, 0u, cls);
+                        } else {
+                            credit(g, out, G.new2old, b, C, cls);
+                        }
                         nsets++;
                     }
-                    // a's and r's credits once per group of lanes holding the same (a, class)
-                    const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
-                    const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                    if (hit && lane == __ffs(grp) - 1) {
-                        credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
-                        hadd(hist_r, cls, (unsigned long long)__popc(grp));
+                    if constexpr (!EDGE) {
+                        // a's and r's credits once per group of lanes holding the same (a, class)
+                        const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
+                        const uint32_t grp = __match_any_sync(0xffffffffu, key);
+                        if (hit && lane == __ffs(grp) - 1) {
+                            credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
+                            hadd(hist_r, cls, (unsigned long long)__popc(grp));
+                        }
                     }
                 }
             }
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                     if (!in_bounds(g, cls < (uint32_t)C)) continue;
                     set3(a, b, ia, -1, eb & 3u, cls);
                 }
-            } else if (!EDGE && VP.s != nullptr && a_end - a_up <= STAGE_A && G.n <= HT_MAX_N) {
+            } else if (VP.s != nullptr && a_end - a_up <= STAGE_A && G.n <= HT_MAX_N) {
                 // Flattened walk of every set with this a, lanes on consecutive
                 // (b, c) work items (short candidate lists would leave most
                 // lanes idle).  b-items: the members of P after a, then the
@@ -559,7 +569,8 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         const int64_t bupo = __shfl_sync(0xffffffffu, b_up, w);
                         const int64_t bendo = __shfl_sync(0xffffffffu, b_end, w);
                         const bool inpo = it0 + w < n1;
-                        uint32_t c = 0u, cls = 255u;
+                        uint32_t c = 0u, cls = 255u, fac_s = 0u, fbc_s = 0u;
+                        int32_t ic = -1;  // position of c in N+(r), else -1 (per-edge credits)
                         if (j < total) {
                             // one path for every shape: the candidate's source (a staged
                             // list or b's row) and which memberships rule it out
@@ -597,21 +608,31 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                             if (!(not_p && frc != 0u) && !(from_b && fac != 0u)) {
                                 const uint32_t fbc = from_b ? (ec & 3u) : search_row(g.col, bupo, bendo, c);
                                 cls = lut[mask4(fra, inpo ? frbo : 0u, frc, fabo, fac, fbc)];
+                                fac_s = fac;
+                                fbc_s = fbc;
+                                ic = not_p ? -1 : sidx;
                             }
                             if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
                         }
                         const bool hit = cls != 255u;
                         if (hit) {
-                            credit(g, out, G.new2old, c, C, cls);
+                            if constexpr (EDGE) {
+                                edge_set<4>(g, E, out, (uint32_t)r, a, bo, c, ia, inpo ? poso : -1, ic, fabo, fac_s,
+                                            fbc_s, cls);
+                            } else {
+                                credit(g, out, G.new2old, c, C, cls);
+                            }
                             nsets++;
                         }
-                        // b's and a's credits once per group of lanes holding the same
-                        // (b, class); r gets a's totals when a is flushed
-                        const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
-                        const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                        if (hit && lane == __ffs(grp) - 1) {
-                            credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
-                            hadd(hist_a, cls, (unsigned long long)__popc(grp));
+                        if constexpr (!EDGE) {
+                            // b's and a's credits once per group of lanes holding the same
+                            // (b, class); r gets a's totals when a is flushed
+                            const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
+                            const uint32_t grp = __match_any_sync(0xffffffffu, key);
+                            if (hit && lane == __ffs(grp) - 1) {
+                                credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
+                                hadd(hist_a, cls, (unsigned long long)__popc(grp));
+                            }
                         }
                     }
                 }
