@@ -294,6 +294,20 @@ __device__ __forceinline__ void ht_insert(uint32_t *ht, uint32_t v, uint32_t bit
     }
 }
 
+// v's bits (0 if absent) and, when present, its slot
+__device__ __forceinline__ uint32_t ht_find_slot(const uint32_t *ht, uint32_t v, uint32_t &slot) {
+    uint32_t h = ht_slot(v);
+    for (int i = 0; i < HT_SLOTS; i++, h = (h + 1u) & (HT_SLOTS - 1)) {
+        const uint32_t cur = ht[h];
+        if (cur == HT_EMPTY) return 0u;
+        if ((cur >> 4) == v) {
+            slot = h;
+            return cur & 15u;
+        }
+    }
+    return 0u;
+}
+
 // v's bits, 0 if absent
 __device__ __forceinline__ uint32_t ht_find(const uint32_t *ht, uint32_t v) {
     uint32_t h = ht_slot(v);
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                 // (h(a, v) << 2) | h(r, v), empty = ~0.  It lives in the warp's
                 // b-histogram area (zero between b's, unused on this walk; 256 of
                 // its 2C words for at most 64 + 128 keys) and is zeroed again after.
-                static_assert(K == 3 || 2 * C >= HT_SLOTS, "the table must fit the b-histogram area");
+                static_assert(K == 3 || 2 * C >= HT_SLOTS + 128, "the table and signatures must fit the b-histogram area");
                 uint32_t *ht = hist_b.lo;
                 for (int i = lane; i < HT_SLOTS; i += 32) ht[i] = HT_EMPTY;
                 __syncwarp();
@@ -519,10 +533,15 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                 __syncwarp();
                 for (int32_t x = lane; x < la; x += 32) ht_insert(ht, NA.s[x] >> 2, (NA.s[x] & 3u) << 2);
                 __syncwarp();
+                // per b-item of a pass: a 128-bit signature of which table slots
+                // (mod 128) hold a neighbour of b -- set by b's own-row items, which
+                // come first, read by the staged-list items, which search b's row only
+                // where their slot's bit is set
+                uint32_t *sig = ht + HT_SLOTS;  // [32][4]
                 for (int32_t it0 = 0; it0 < nitems; it0 += 32) {
                     const int32_t it = it0 + lane;
                     uint32_t b = 0u, frb = 0u, fab = 0u;
-                    int32_t cnt = 0, pos = 0;  // position of b in P, or in N(a) above r
+                    int32_t cnt0 = 0, cnt1 = 0, pos = 0;  // items from b's row / from the staged lists
                     int64_t b_up = 0, b_end = 0;
                     if (it < nitems) {
                         const bool inp = it < n1;
@@ -543,101 +562,112 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                             b_end = __ldg(g.rowptr + b + 1);
                             if (in_bounds(g, bb >= 0 && bb <= b_end && b_end <= G.nnz)) {
                                 b_up = upper_row(g.col, bb, b_end, (uint32_t)r);
-                                const int32_t lb = (int32_t)(b_end - b_up);
-                                cnt = inp ? (L - 1 - pos) + la + lb : (la - pos - 1) + lb;
+                                cnt0 = (int32_t)(b_end - b_up);
+                                cnt1 = inp ? (L - 1 - pos) + la : (la - pos - 1);
                             }
                         }
                     }
-                    int32_t incl = cnt;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                    for (int32_t j0 = 0; j0 < total; j0 += 32) {
-                        const int32_t j = j0 + lane;
-                        int32_t w = 0;
+                    for (int q = 0; q < 4; q++) sig[lane * 4 + q] = 0u;
+                    __syncwarp();
+                    for (int grp = 0; grp < 2; grp++) {
+                        const int32_t cnt = grp == 0 ? cnt0 : cnt1;
+                        int32_t incl = cnt;
 #pragma unroll
-                        for (int sh = 16; sh >= 1; sh >>= 1)
-                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
-                        const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
-                        const uint32_t frbo = __shfl_sync(0xffffffffu, frb, w);
-                        const uint32_t fabo = __shfl_sync(0xffffffffu, fab, w);
-                        const int32_t poso = __shfl_sync(0xffffffffu, pos, w);
-                        const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
-                        const int64_t bupo = __shfl_sync(0xffffffffu, b_up, w);
-                        const int64_t bendo = __shfl_sync(0xffffffffu, b_end, w);
-                        const bool inpo = it0 + w < n1;
-                        uint32_t c = 0u, cls = 255u, fac_s = 0u, fbc_s = 0u;
-                        int32_t ic = -1;  // position of c in N+(r), else -1 (per-edge credits)
-                        if (j < total) {
-                            // one path for every shape: the candidate's source (a staged
-                            // list or b's row) and which memberships rule it out
-                            //   b in P:   P after b (1,1,1) | N(a) \ P (1,1,2) | N(b) \ N(a) \ P (1,1,2)
-                            //   b deeper: N(a) \ P after b (1,2,2) | N(b) \ (N(a) u P) (1,2,3)
-                            int32_t off = j - start, sidx = 0;
-                            int64_t gidx = 0;
-                            bool from_b = false, not_p = true;
-                            if (inpo) {
-                                const int32_t n111 = L - 1 - poso;
-                                if (off < n111) {
-                                    sidx = poso + 1 + off;
-                                    not_p = false;
-                                } else if ((off -= n111) < la) {
-                                    sidx = STAGE_P + off;
-                                } else {
-                                    gidx = bupo + (off - la);
-                                    from_b = true;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                        for (int32_t j0 = 0; j0 < total; j0 += 32) {
+                            const int32_t j = j0 + lane;
+                            int32_t w = 0;
+#pragma unroll
+                            for (int sh = 16; sh >= 1; sh >>= 1)
+                                if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                            const uint32_t bo = __shfl_sync(0xffffffffu, b, w);
+                            const uint32_t frbo = __shfl_sync(0xffffffffu, frb, w);
+                            const uint32_t fabo = __shfl_sync(0xffffffffu, fab, w);
+                            const int32_t poso = __shfl_sync(0xffffffffu, pos, w);
+                            const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
+                            const int64_t bupo = __shfl_sync(0xffffffffu, b_up, w);
+                            const int64_t bendo = __shfl_sync(0xffffffffu, b_end, w);
+                            const bool inpo = it0 + w < n1;
+                            uint32_t c = 0u, cls = 255u, fac_s = 0u, fbc_s = 0u;
+                            int32_t ic = -1;  // position of c in N+(r), else -1 (per-edge credits)
+                            if (j < total) {
+                                // one path for every shape: the candidate's source and which
+                                // memberships rule it out
+                                //   b's row:      N(b) \ N(a) \ P (1,1,2) | N(b) \ (N(a) u P) (1,2,3)
+                                //   staged lists: b in P: P after b (1,1,1) | N(a) \ P (1,1,2);
+                                //                 b deeper: N(a) \ P after b (1,2,2)
+                                const int32_t off = j - start;
+                                int32_t sidx = 0;
+                                bool not_p = true;
+                                if (grp == 1) {
+                                    if (inpo) {
+                                        const int32_t n111 = L - 1 - poso;
+                                        if (off < n111) {
+                                            sidx = poso + 1 + off;
+                                            not_p = false;
+                                        } else {
+                                            sidx = STAGE_P + (off - n111);
+                                        }
+                                    } else {
+                                        sidx = STAGE_P + poso + 1 + off;
+                                    }
                                 }
-                            } else {
-                                const int32_t n122 = la - poso - 1;
-                                if (off < n122) {
-                                    sidx = STAGE_P + poso + 1 + off;
+                                const uint32_t ec = grp == 0 ? __ldg(g.col + bupo + off) : lists[sidx];
+                                c = ec >> 2;
+                                uint32_t slot = 0u;
+                                const uint32_t hc = ht_find_slot(ht, c, slot);
+                                const uint32_t frc = hc & 3u, fac = hc >> 2;
+                                if (grp == 0) {
+                                    if (hc != 0u) {
+                                        // c in P or N(a) and adjacent to b: not a set here, but
+                                        // b's signature learns of it
+                                        atomicOr(sig + w * 4 + ((slot >> 5) & 3u), 1u << (slot & 31u));
+                                    } else {
+                                        fbc_s = ec & 3u;
+                                        cls = lut[mask4(fra, inpo ? frbo : 0u, 0u, fabo, 0u, fbc_s)];
+                                    }
+                                } else if (!(not_p && frc != 0u)) {
+                                    // a candidate from N(a) must not be in P
+                                    const uint32_t sb = sig[w * 4 + ((slot >> 5) & 3u)];
+                                    const uint32_t fbc = ((sb >> (slot & 31u)) & 1u) ? search_row(g.col, bupo, bendo, c) : 0u;
+                                    cls = lut[mask4(fra, inpo ? frbo : 0u, frc, fabo, fac, fbc)];
+                                    fac_s = fac;
+                                    fbc_s = fbc;
+                                    ic = not_p ? -1 : sidx;
+                                }
+                                if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
+                            }
+                            const bool hit = cls != 255u;
+                            if (hit) {
+                                if constexpr (EDGE) {
+                                    edge_set<4>(g, E, out, (uint32_t)r, a, bo, c, ia, inpo ? poso : -1, ic, fabo, fac_s,
+                                                fbc_s, cls);
                                 } else {
-                                    gidx = bupo + (off - n122);
-                                    from_b = true;
+                                    credit(g, out, G.new2old, c, C, cls);
+                                }
+                                nsets++;
+                            }
+                            if constexpr (!EDGE) {
+                                // b's and a's credits once per group of lanes holding the same
+                                // (b, class); r gets a's totals when a is flushed
+                                const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
+                                const uint32_t grpm = __match_any_sync(0xffffffffu, key);
+                                if (hit && lane == __ffs(grpm) - 1) {
+                                    credit_n(g, out, G.new2old, bo, C, cls, __popc(grpm));
+                                    hadd(hist_a, cls, (unsigned long long)__popc(grpm));
                                 }
                             }
-                            const uint32_t ec = from_b ? __ldg(g.col + gidx) : lists[sidx];
-                            c = ec >> 2;
-                            const uint32_t hc = ht_find(ht, c);
-                            const uint32_t frc = hc & 3u, fac = hc >> 2;
-                            // a candidate from b's row must be in neither list; one from N(a)
-                            // must not be in P
-                            if (!(not_p && frc != 0u) && !(from_b && fac != 0u)) {
-                                const uint32_t fbc = from_b ? (ec & 3u) : search_row(g.col, bupo, bendo, c);
-                                cls = lut[mask4(fra, inpo ? frbo : 0u, frc, fabo, fac, fbc)];
-                                fac_s = fac;
-                                fbc_s = fbc;
-                                ic = not_p ? -1 : sidx;
-                            }
-                            if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
                         }
-                        const bool hit = cls != 255u;
-                        if (hit) {
-                            if constexpr (EDGE) {
-                                edge_set<4>(g, E, out, (uint32_t)r, a, bo, c, ia, inpo ? poso : -1, ic, fabo, fac_s,
-                                            fbc_s, cls);
-                            } else {
-                                credit(g, out, G.new2old, c, C, cls);
-                            }
-                            nsets++;
-                        }
-                        if constexpr (!EDGE) {
-                            // b's and a's credits once per group of lanes holding the same
-                            // (b, class); r gets a's totals when a is flushed
-                            const unsigned long long key = hit ? (((unsigned long long)bo << 8) | cls) : (~0ull - lane);
-                            const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                            if (hit && lane == __ffs(grp) - 1) {
-                                credit_n(g, out, G.new2old, bo, C, cls, __popc(grp));
-                                hadd(hist_a, cls, (unsigned long long)__popc(grp));
-                            }
-                        }
+                        __syncwarp();  // b's signatures complete before the staged-list items
                     }
                 }
                 __syncwarp();
-                for (int i = lane; i < HT_SLOTS; i += 32) ht[i] = 0u;  // the b-histogram again
+                for (int i = lane; i < HT_SLOTS + 128; i += 32) ht[i] = 0u;  // the b-histogram again
                 __syncwarp();
             } else {
                 // (A1) b in P after a
