@@ -209,6 +209,7 @@ __device__ __forceinline__ void edge_set(const Csr &g, const EdgeDesc &E, uint64
 // and the copies cost more than they save).
 constexpr int STAGE_P = 64, STAGE_A = 128;
 constexpr int STAGE_WORDS = STAGE_P + STAGE_A;  // per warp
+static_assert(STAGE_A >= 32 * 4, "the k = 3 walk keeps 4 words of star flags per a-item in the N(a) area");
 
 struct View {
     const uint32_t *s;  // staged entries (shared memory), or nullptr
@@ -226,6 +227,21 @@ __device__ __forceinline__ View stage(const Csr &g, uint32_t *dst, int64_t beg, 
 
 __device__ __forceinline__ uint32_t view_entry(const Csr &g, const View &v, int64_t x) {
     return v.s ? v.s[x - v.beg] : __ldg(g.col + x);
+}
+
+// position of u in a staged view, -1 if absent
+__device__ __forceinline__ int32_t view_pos(const View &v, uint32_t u) {
+    int32_t lo = 0, len = (int32_t)(v.end - v.beg);
+    while (len > 0) {
+        const int32_t half = len >> 1;
+        if ((v.s[lo + half] >> 2) < u) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo < (int32_t)(v.end - v.beg) && (v.s[lo] >> 2) == u ? lo : -1;
 }
 
 // flags of neighbour u in the view (0 if absent)
@@ -400,10 +416,15 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
             // consecutive (a, b) items.  Credits to a are combined over the
             // lanes holding the same (a, class).
             const int32_t na = task.j < L ? (L - 1 - task.j) / task.stride + 1 : 0;
+            // per a-item of a pass: h(a, x) for every member x of P (2 bits per
+            // position, at most 64 positions: 4 words), in the warp's N(a) staging
+            // area, which this walk does not use -- set by a's own-row items, which
+            // come first, and read by the star items, which then search no row
+            uint32_t *fmask = lists + STAGE_P;  // [32][4]
             for (int32_t it0 = 0; it0 < na; it0 += 32) {
                 const int32_t it = it0 + lane;
                 uint32_t a = 0u, fra = 0u;
-                int32_t ia = 0, cnt = 0;
+                int32_t ia = 0, cnt0 = 0, cnt1 = 0;  // items from a's row / star items
                 int64_t a_up = 0, a_end = 0;
                 if (it < na) {
                     ia = task.j + it * task.stride;
@@ -415,65 +436,78 @@ __global__ void __launch_bounds__(256, 4) count_kernel(GraphDesc single, const G
                         a_end = __ldg(g.rowptr + a + 1);
                         if (in_bounds(g, ab >= 0 && ab <= a_end && a_end <= G.nnz)) {
                             a_up = upper_row(g.col, ab, a_end, (uint32_t)r);
-                            cnt = (L - 1 - ia) + (int32_t)(a_end - a_up);
+                            cnt0 = (int32_t)(a_end - a_up);
+                            cnt1 = L - 1 - ia;
                         }
                     }
                 }
-                int32_t incl = cnt;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                for (int32_t j0 = 0; j0 < total; j0 += 32) {
-                    const int32_t j = j0 + lane;
-                    int32_t w = 0;
+                for (int q = 0; q < 4; q++) fmask[lane * 4 + q] = 0u;
+                __syncwarp();
+                for (int grp = 0; grp < 2; grp++) {
+                    const int32_t cnt = grp == 0 ? cnt0 : cnt1;
+                    int32_t incl = cnt;
 #pragma unroll
-                    for (int sh = 16; sh >= 1; sh >>= 1)
-                        if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
-                    const uint32_t ao = __shfl_sync(0xffffffffu, a, w);
-                    const uint32_t frao = __shfl_sync(0xffffffffu, fra, w);
-                    const int32_t iao = __shfl_sync(0xffffffffu, ia, w);
-                    const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
-                    const int64_t aupo = __shfl_sync(0xffffffffu, a_up, w);
-                    const int64_t aendo = __shfl_sync(0xffffffffu, a_end, w);
-                    uint32_t b = 0u, cls = 255u, fab = 0u;
-                    int32_t ib = -1;  // position of b in N+(r) (star), else -1
-                    if (j < total) {
-                        const int32_t off = j - start, nstar = L - 1 - iao;
-                        if (off < nstar) {  // star: b in P after a
-                            ib = iao + 1 + off;
-                            const uint32_t eb = VP.s[ib];
-                            b = eb >> 2;
-                            fab = search_row(g.col, aupo, aendo, b);
-                            cls = lut[mask3(frao, eb & 3u, fab)];
-                        } else {  // path: b in N(a) \ N(r)
-                            const uint32_t eb = __ldg(g.col + aupo + (off - nstar));
-                            b = eb >> 2;
-                            fab = eb & 3u;
-                            if (!view_find(g, VP, b)) cls = lut[mask3(frao, 0u, fab)];
-                        }
-                        if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
                     }
-                    const bool hit = cls != 255u;
-                    if (hit) {
-                        if constexpr (EDGE) {
-                            edge_set<3>(g, E, out, (uint32_t)r, ao, b, 0u, iao, ib, -1, fab, 0u, 0u, cls);
-                        } else {
-                            credit(g, out, G.new2old, b, C, cls);
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    for (int32_t j0 = 0; j0 < total; j0 += 32) {
+                        const int32_t j = j0 + lane;
+                        int32_t w = 0;
+#pragma unroll
+                        for (int sh = 16; sh >= 1; sh >>= 1)
+                            if (__shfl_sync(0xffffffffu, incl, w + sh - 1) <= j) w += sh;
+                        const uint32_t ao = __shfl_sync(0xffffffffu, a, w);
+                        const uint32_t frao = __shfl_sync(0xffffffffu, fra, w);
+                        const int32_t iao = __shfl_sync(0xffffffffu, ia, w);
+                        const int32_t start = __shfl_sync(0xffffffffu, incl, w) - __shfl_sync(0xffffffffu, cnt, w);
+                        const int64_t aupo = __shfl_sync(0xffffffffu, a_up, w);
+                        uint32_t b = 0u, cls = 255u, fab = 0u;
+                        int32_t ib = -1;  // position of b in N+(r) (star), else -1
+                        if (j < total) {
+                            const int32_t off = j - start;
+                            if (grp == 0) {  // path: b in N(a) above r, not in P
+                                const uint32_t eb = __ldg(g.col + aupo + off);
+                                b = eb >> 2;
+                                fab = eb & 3u;
+                                const int32_t px = view_pos(VP, b);
+                                if (px >= 0) {
+                                    // b in P and adjacent to a: a star's flag, not a path
+                                    atomicOr(fmask + w * 4 + (px >> 4), fab << ((px & 15) * 2));
+                                } else {
+                                    cls = lut[mask3(frao, 0u, fab)];
+                                }
+                            } else {  // star: b in P after a
+                                ib = iao + 1 + off;
+                                const uint32_t eb = VP.s[ib];
+                                b = eb >> 2;
+                                fab = (fmask[w * 4 + (ib >> 4)] >> ((ib & 15) * 2)) & 3u;
+                                cls = lut[mask3(frao, eb & 3u, fab)];
+                            }
+                            if (cls != 255u && !in_bounds(g, cls < (uint32_t)C)) cls = 255u;
                         }
-                        nsets++;
-                    }
-                    if constexpr (!EDGE) {
-                        // a's and r's credits once per group of lanes holding the same (a, class)
-                        const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
-                        const uint32_t grp = __match_any_sync(0xffffffffu, key);
-                        if (hit && lane == __ffs(grp) - 1) {
-                            credit_n(g, out, G.new2old, ao, C, cls, __popc(grp));
-                            hadd(hist_r, cls, (unsigned long long)__popc(grp));
+                        const bool hit = cls != 255u;
+                        if (hit) {
+                            if constexpr (EDGE) {
+                                edge_set<3>(g, E, out, (uint32_t)r, ao, b, 0u, iao, ib, -1, fab, 0u, 0u, cls);
+                            } else {
+                                credit(g, out, G.new2old, b, C, cls);
+                            }
+                            nsets++;
+                        }
+                        if constexpr (!EDGE) {
+                            // a's and r's credits once per group of lanes holding the same (a, class)
+                            const unsigned long long key = hit ? (((unsigned long long)ao << 8) | cls) : (~0ull - lane);
+                            const uint32_t grpm = __match_any_sync(0xffffffffu, key);
+                            if (hit && lane == __ffs(grpm) - 1) {
+                                credit_n(g, out, G.new2old, ao, C, cls, __popc(grpm));
+                                hadd(hist_r, cls, (unsigned long long)__popc(grpm));
+                            }
                         }
                     }
+                    __syncwarp();  // a's flags complete before the star items
                 }
             }
         } else
