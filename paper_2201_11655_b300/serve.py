@@ -56,10 +56,11 @@ def footprint_bytes(n: int, m: int, k: int, hub_slots: int = 148) -> int:
     vertex plus 8 per arc), the output (8 * C_k per vertex), the rank-space
     credit accumulator (8 * 199 per vertex) and, for k = 4, the depth-3
     credit columns (8 * 16 per vertex), and the scratch of the root-per-CTA
-    kernel (per slot: a position map of 4 bytes per vertex and ~60 bytes per
-    distinct second-hop vertex, at most min(n, 2m))."""
+    kernel (per slot: a position map of 4 bytes per vertex and ~76 bytes per
+    distinct second-hop vertex, at most min(n, 2m): 12 counters, its id, its
+    NP-list offset, its row bounds, and a share of the NP and H lists)."""
     slots = max(1, min(hub_slots, n // 64))
-    hub = slots * (4 * n + 60 * min(n, 2 * m)) if n >= 64 else 0
+    hub = slots * (4 * n + 76 * min(n, 2 * m)) if n >= 64 else 0
     acc = 8 * 199 * n + (8 * 16 * n if k == 4 else 0)
     return int(80 * m + 48 * n + 8 * C_K[k] * n + acc + hub + (1 << 20))
 
